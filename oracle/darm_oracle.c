@@ -1,0 +1,226 @@
+/*
+ * CPU oracle for the bitonic compare-exchange network of DARM's running
+ * example (Saumya, Sundararajah, Kulkarni, "DARM: Control-Flow Melding for
+ * SIMT Thread Divergence Reduction", Fig. 1 and Section III).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: only the tests, the smoke check and the benchmark's CPU
+ * baseline use it.  It shares no code, header, table or helper with the CUDA
+ * library; the two are written independently so that one can check the other.
+ *
+ * Everything here is deliberately plain, single-threaded and slow:
+ *
+ *   - oracle_bitonic_{u32,u64}: the iterative network of Fig. 1, written
+ *     with the same loop nest (k doubles from 2 to n, j halves from k/2 to 1,
+ *     partner l = i ^ j, the lower index of a pair decides), generalised
+ *     from "one element per thread" to a sequential loop over i.
+ *   - oracle_bitonic_rec_{u32,u64}: an independent recursive formulation of
+ *     the same comparator network (Batcher's sort/merge recursion), used to
+ *     pin payload order under duplicate keys.
+ *   - oracle_bitonic_f32: float keys through the IEEE-754 totalOrder bit map
+ *     (not in the paper, whose keys are int; documented reading).
+ *   - oracle_segmented_{u32,u64}: independent segments of power-of-two
+ *     capacity, padded beyond their real length with the direction's
+ *     extreme key before the network runs.
+ *
+ * Readings of the paper taken here (the paper is silent on them):
+ *   - descending order flips every comparator: the ascending test of Fig. 1
+ *     becomes ((i & k) == 0) XOR desc;
+ *   - a swap happens only on strict inequality (Fig. 1 compares with < on the
+ *     ascending side and > on the descending side), so equal keys never move
+ *     relative to each other inside one comparator;
+ *   - a payload travels with its key; only keys are compared.
+ *
+ * Status codes: 0 ok, 2 length not a power of two.
+ */
+#include <stddef.h>
+#include <stdint.h>
+#include <string.h>
+
+#define ORACLE_OK 0
+#define ORACLE_ERR_NOT_POW2 2
+
+static int is_pow2_u64(uint64_t n) { return n != 0 && (n & (n - 1)) == 0; }
+
+#ifndef DARM_ORACLE_MUTANT
+#define DARM_ORACLE_MUTANT 0
+#endif
+
+/*
+ * Iterative network of Fig. 1.  For every stage k and every layer j, each
+ * index i whose partner l = i ^ j lies above it compares (key[i], key[l]).
+ * The block of size k that i belongs to runs ascending when bit k of i is
+ * clear (Fig. 1's "(tid & k) == 0" test), flipped for a descending sort.
+ * Ascending side: swap when key[l] < key[i]; descending side: swap when
+ * key[l] > key[i].  `val` may be NULL (keys only).
+ *
+ * DARM_ORACLE_MUTANT (0 in every real build) plants one plausible mistake at
+ * compile time so that the tests can show that the pins catch it:
+ *   1 direction taken from bit j instead of bit k
+ *   2 non-strict comparison (<= / >=)
+ *   3 payload not swapped with its key
+ *   4 descending flag ignored
+ *   5 layer loop stops one layer early (j > 1)
+ */
+#define DEFINE_ITERATIVE(NAME, KT)                                             \
+  int NAME(KT* key, uint32_t* val, uint64_t n, int desc) {                     \
+    if (n <= 1) return ORACLE_OK;                                              \
+    if (!is_pow2_u64(n)) return ORACLE_ERR_NOT_POW2;                           \
+    for (uint64_t k = 2; k <= n; k <<= 1) {                                    \
+      for (uint64_t j = k >> 1; j > (DARM_ORACLE_MUTANT == 5 ? 1u : 0u);       \
+           j >>= 1) {                                                          \
+        for (uint64_t i = 0; i < n; ++i) {                                     \
+          uint64_t l = i ^ j;                                                  \
+          if (l <= i) continue;                                                \
+          uint64_t dirbit = (DARM_ORACLE_MUTANT == 1) ? (i & j) : (i & k);     \
+          int up = (dirbit == 0);                                              \
+          if (DARM_ORACLE_MUTANT != 4 && desc) up = !up;                       \
+          int do_swap;                                                         \
+          if (DARM_ORACLE_MUTANT == 2)                                         \
+            do_swap = up ? (key[l] <= key[i]) : (key[l] >= key[i]);            \
+          else                                                                 \
+            do_swap = up ? (key[l] < key[i]) : (key[l] > key[i]);              \
+          if (do_swap) {                                                       \
+            KT tk = key[i];                                                    \
+            key[i] = key[l];                                                   \
+            key[l] = tk;                                                       \
+            if (val && DARM_ORACLE_MUTANT != 3) {                              \
+              uint32_t tv = val[i];                                            \
+              val[i] = val[l];                                                 \
+              val[l] = tv;                                                     \
+            }                                                                  \
+          }                                                                    \
+        }                                                                      \
+      }                                                                        \
+    }                                                                          \
+    return ORACLE_OK;                                                          \
+  }
+
+DEFINE_ITERATIVE(oracle_bitonic_u32, uint32_t)
+DEFINE_ITERATIVE(oracle_bitonic_u64, uint64_t)
+
+/*
+ * Recursive formulation (Batcher's bitonic sorter) of the same network.
+ * rec_sort(lo, n, up) sorts key[lo .. lo+n) in direction `up`: it sorts the
+ * lower half ascending and the upper half descending (in Fig. 1 the halves
+ * of a size-k block always take these two directions, whatever the block's
+ * own direction), then merges.  rec_merge(lo, n, up) compares (i, i + n/2)
+ * for every i in the lower half, then merges both halves in the same
+ * direction.  A descending sort flips every direction.  Comparators of one
+ * layer touch disjoint pairs, so the depth-first order gives the same result
+ * as the layer-by-layer order of Fig. 1 whenever both describe the same
+ * comparator set.
+ */
+#define DEFINE_RECURSIVE(NAME, KT)                                             \
+  static void NAME##_merge(KT* key, uint32_t* val, uint64_t lo, uint64_t n,    \
+                           int up) {                                           \
+    if (n < 2) return;                                                         \
+    uint64_t h = n / 2;                                                        \
+    for (uint64_t i = lo; i < lo + h; ++i) {                                   \
+      uint64_t l = i + h;                                                      \
+      int do_swap = up ? (key[l] < key[i]) : (key[l] > key[i]);                \
+      if (do_swap) {                                                           \
+        KT tk = key[i];                                                        \
+        key[i] = key[l];                                                       \
+        key[l] = tk;                                                           \
+        if (val) {                                                             \
+          uint32_t tv = val[i];                                                \
+          val[i] = val[l];                                                     \
+          val[l] = tv;                                                         \
+        }                                                                      \
+      }                                                                        \
+    }                                                                          \
+    NAME##_merge(key, val, lo, h, up);                                         \
+    NAME##_merge(key, val, lo + h, h, up);                                     \
+  }                                                                            \
+  static void NAME##_sort(KT* key, uint32_t* val, uint64_t lo, uint64_t n,     \
+                          int up, int desc) {                                  \
+    if (n < 2) return;                                                         \
+    uint64_t h = n / 2;                                                        \
+    NAME##_sort(key, val, lo, h, !desc, desc);                                 \
+    NAME##_sort(key, val, lo + h, h, desc, desc);                              \
+    NAME##_merge(key, val, lo, n, up);                                         \
+  }                                                                            \
+  int NAME(KT* key, uint32_t* val, uint64_t n, int desc) {                     \
+    if (n <= 1) return ORACLE_OK;                                              \
+    if (!is_pow2_u64(n)) return ORACLE_ERR_NOT_POW2;                           \
+    NAME##_sort(key, val, 0, n, !desc, desc);                                  \
+    return ORACLE_OK;                                                          \
+  }
+
+DEFINE_RECURSIVE(oracle_bitonic_rec_u32, uint32_t)
+DEFINE_RECURSIVE(oracle_bitonic_rec_u64, uint64_t)
+
+/*
+ * Float keys.  The paper sorts int keys; float keys are ordered here by the
+ * IEEE-754 totalOrder of their bit patterns (for non-NaN values): a
+ * non-negative float gets its sign bit set, a negative float has every bit
+ * inverted, so that unsigned order of the mapped word is numeric order with
+ * -0.0 placed just below +0.0.  The mapped words go through the u32 network
+ * and are mapped back.
+ */
+static uint32_t total_order_bits(uint32_t u) {
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+static uint32_t total_order_bits_inverse(uint32_t m) {
+  return (m & 0x80000000u) ? (m & 0x7FFFFFFFu) : ~m;
+}
+
+int oracle_bitonic_f32(float* key, uint32_t* val, uint64_t n, int desc) {
+  if (n <= 1) return ORACLE_OK;
+  if (!is_pow2_u64(n)) return ORACLE_ERR_NOT_POW2;
+  uint32_t* w = (uint32_t*)key; /* same storage, reinterpreted */
+  for (uint64_t i = 0; i < n; ++i) {
+    uint32_t u;
+    memcpy(&u, &key[i], sizeof u);
+    u = total_order_bits(u);
+    w[i] = u;
+  }
+  int rc = oracle_bitonic_u32(w, val, n, desc);
+  for (uint64_t i = 0; i < n; ++i) {
+    uint32_t u = total_order_bits_inverse(w[i]);
+    memcpy(&key[i], &u, sizeof u);
+  }
+  return rc;
+}
+
+/*
+ * Segmented sort: segment s occupies [off[s], off[s+1]) of key/val; its
+ * capacity off[s+1] - off[s] must be a power of two (paper: NUM is a power
+ * of two).  Elements from len[s] up to the capacity are overwritten with the
+ * sentinel (the largest key for ascending, 0 for descending; payload
+ * 0xFFFFFFFF) and the whole capacity is sorted by the network of Fig. 1 with
+ * indices local to the segment.  desc_per_seg may be NULL (all use `desc`).
+ */
+#define DEFINE_SEGMENTED(NAME, KT, NET, KMAX)                                  \
+  int NAME(KT* key, uint32_t* val, const uint64_t* off, const uint32_t* len,   \
+           uint64_t nseg, int desc, const uint8_t* desc_per_seg) {             \
+    for (uint64_t s = 0; s < nseg; ++s) {                                      \
+      uint64_t cap = off[s + 1] - off[s];                                      \
+      if (cap == 0) continue;                                                  \
+      if (!is_pow2_u64(cap)) return ORACLE_ERR_NOT_POW2;                       \
+      int d = desc_per_seg ? (desc_per_seg[s] != 0) : (desc != 0);             \
+      KT sentinel = d ? (KT)0 : (KT)KMAX;                                      \
+      for (uint64_t i = len[s]; i < cap; ++i) {                                \
+        key[off[s] + i] = sentinel;                                            \
+        if (val) val[off[s] + i] = 0xFFFFFFFFu;                                \
+      }                                                                        \
+      int rc = NET(key + off[s], val ? val + off[s] : NULL, cap, d);           \
+      if (rc) return rc;                                                       \
+    }                                                                          \
+    return ORACLE_OK;                                                          \
+  }
+
+DEFINE_SEGMENTED(oracle_segmented_u32, uint32_t, oracle_bitonic_u32, 0xFFFFFFFFu)
+DEFINE_SEGMENTED(oracle_segmented_u64, uint64_t, oracle_bitonic_u64,
+                 0xFFFFFFFFFFFFFFFFull)
+
+/* Number of compare-exchange evaluations of the network for n = 2^m:
+ * (n/2) * m(m+1)/2.  Used only to scale timing figures. */
+uint64_t oracle_compare_exchanges(uint64_t n) {
+  uint64_t m = 0;
+  while ((1ull << m) < n) ++m;
+  return (n / 2) * (m * (m + 1) / 2);
+}
+
+int oracle_mutant_id(void) { return DARM_ORACLE_MUTANT; }
