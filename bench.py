@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Benchmark: sorted keys/s of the bitonic network, melded vs divergent kernels.
+
+One step = one whole sort (every pass of the network) of one synthetic array
+already resident in HBM.  Default workload: key-value sort of 2^24 uniform
+uint32 keys with a uint32 payload (payload = index).  `--workload f32` runs
+2^26 float32 keys (N(0,1) with duplicates and signed zeros).
+
+Prints ONE JSON line on rank 0.  Under torchrun (N > 1) every rank sorts its
+own replica (the network of one array does not shard without an exchange
+step): weak scaling, value = arrays sorted by all ranks / max time.
+
+--impl reference times the CPU oracle (single-threaded plain C of the
+same network) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sorted keys/s, melded vs divergent bitonic kernel; warp exec efficiency"
+L2_FLUSH_BYTES = 256 << 20  # larger than the 126 MiB L2
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["darm", "reference"], default="darm")
+    ap.add_argument("--workload", choices=["kv24", "kv24skew", "f32"], default="kv24")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    """(description, keys, vals, dtype label) for a workload name."""
+    import synth
+    if name == "kv24":
+        k, v = synth.cfg2_kv(skew=False)
+        return ("bitonic key-value sort, 2^24 uint32 keys uniform, uint32 payload = index", k, v)
+    if name == "kv24skew":
+        k, v = synth.cfg2_kv(skew=True)
+        return ("bitonic key-value sort, 2^24 uint32 keys = rand mod 16, uint32 payload = index",
+                k, v)
+    k = synth.cfg3_f32()
+    return ("bitonic sort, 2^26 float32 keys N(0,1) with 1% duplicates and signed zeros", k, None)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples taken while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, world, rank):
+    """CPU oracle on a bounded sample of the workload (rank 0 only)."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    desc, keys, vals = workload(args.workload)
+    n_full = keys.size
+    # bounded sample: a power-of-two prefix of the same array, sized so that
+    # W + K sorts stay within a few minutes on one core
+    budget_s = 150.0
+    per_ce_ns = 4.5
+    steps = args.steps + args.warmup
+    m = int(np.log2(n_full))
+    while m > 10 and oracle.compare_exchanges(1 << m) * per_ce_ns * 1e-9 * steps > budget_s:
+        m -= 1
+    n = 1 << m
+    ks = keys[:n].copy()
+    vs = None if vals is None else vals[:n].copy()
+    for _ in range(args.warmup):
+        oracle.bitonic_sort(ks, vs)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.bitonic_sort(ks, vs)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = n / dt
+    sample = f"first 2^{m} elements of the {n_full}-element array, one oracle sort per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "keys/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if vals is None and keys.dtype == np.float32 else
+        "u32", "data": "synthetic",
+        "config": {"workload": desc, "n": n_full},
+        "cpu_baseline": {"value": value, "unit": "keys/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(keys, vals):
+    """Oracle keys/s on a bounded sample (about 10-20 s of one core)."""
+    import numpy as np
+
+    import oracle
+    n_full = keys.size
+    m = int(np.log2(n_full))
+    while m > 12 and oracle.compare_exchanges(1 << m) * 4.5e-9 > 15.0:
+        m -= 1
+    n = 1 << m
+    ks = keys[:n].copy()
+    vs = None if vals is None else vals[:n].copy()
+    t0 = time.perf_counter()
+    oracle.bitonic_sort(ks, vs)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
+            "sample": f"one single-threaded oracle sort of the first 2^{m} elements "
+                      f"({dt:.1f} s)"}
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import numpy as np
+    import torch
+
+    import paper_2107_05681_gb300 as darm
+
+    torch.cuda.set_device(local)
+    darm.init(local)
+    desc, keys_np, vals_np = workload(args.workload)
+    n = keys_np.size
+    has_vals = vals_np is not None
+    dtype_code = darm.F32 if keys_np.dtype == np.float32 else darm.U32
+    elem_bytes = keys_np.itemsize + (4 if has_vals else 0)
+
+    src_k = torch.from_numpy(keys_np).cuda()
+    src_v = torch.from_numpy(vals_np).cuda() if has_vals else None
+    work_k = torch.empty_like(src_k)
+    work_v = torch.empty_like(src_v) if has_vals else None
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def reset():
+        work_k.copy_(src_k)
+        if has_vals:
+            work_v.copy_(src_v)
+        flush.fill_(1.0)  # evicts the array from L2 between steps
+
+    def timed_steps(variant, steps, warmup):
+        for _ in range(warmup):
+            reset()
+            darm.sort(work_k, work_v, variant=variant)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        l0 = darm.launch_count()
+        for a, b in evs:
+            reset()
+            a.record(stream)
+            darm.sort(work_k, work_v, variant=variant)
+            b.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        launches = darm.launch_count() - l0
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        return ms, launches
+
+    # correctness guard on the timed configuration (cheap properties; the
+    # element-by-element parity against the oracle lives in the tests)
+    reset()
+    darm.sort(work_k, work_v, variant="melded")
+    torch.cuda.synchronize()
+    got = work_k.cpu().numpy()
+    if keys_np.dtype == np.float32:
+        gw = got.view(np.uint32)
+        mapped = np.where(gw >> 31, gw ^ np.uint32(0x80000000), ~gw)
+        assert np.all(mapped[1:] >= mapped[:-1]), "result not sorted"
+    else:
+        assert np.all(got[1:] >= got[:-1]), "result not sorted"
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_meld, launches_meld = timed_steps("melded", args.steps, args.warmup)
+    ms_div, launches_div = timed_steps("divergent", args.steps, args.warmup)
+    clk = clocks.stop()
+    ms_meld = max_over_ranks(ms_meld, world)
+    ms_div = max_over_ranks(ms_div, world)
+    value = world * n * args.steps / (ms_meld * 1e-3)
+    value_div = world * n * args.steps / (ms_div * 1e-3)
+
+    # per-launch timing for the roofline of the dominant pass kind
+    passes, launches_per_sort, tile = darm.plan_info(dtype_code, n, has_vals, "melded")
+    per_kind = {}
+    for _ in range(args.steps):
+        reset()
+        for name, t in darm.sort_profile(work_k, work_v, variant="melded"):
+            per_kind.setdefault(name, []).append(t)
+    totals = {k: sum(v) for k, v in per_kind.items()}
+    dom = max(totals, key=totals.get)
+    avg_ms = statistics.mean(per_kind[dom])
+    bytes_per_launch = 2 * n * elem_bytes  # each pass reads and writes the array once
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    peak = None
+    peak_src = "measured"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        peak = 6800.0
+        peak_src = "fallback"
+    whole_sort_gbs = bytes_per_launch * passes / (ms_meld / args.steps * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        hk = torch.empty(n, dtype=src_k.dtype, pin_memory=True).numpy()
+        hv = torch.empty(n, dtype=torch.uint32, pin_memory=True).numpy() if has_vals else None
+        for _ in range(2):
+            hk[:] = keys_np
+            if has_vals:
+                hv[:] = vals_np
+            darm.sort_host(hk, hv, variant="melded")
+        tot = 0.0
+        for _ in range(args.steps):
+            hk[:] = keys_np
+            if has_vals:
+                hv[:] = vals_np
+            t0 = time.perf_counter()
+            darm.sort_host(hk, hv, variant="melded")
+            tot += time.perf_counter() - t0
+        tot = max_over_ranks(tot, world)
+        e2e = {"value": world * n * args.steps / tot, "unit": "keys/s",
+               "h2d_bytes_per_step": n * elem_bytes, "d2h_bytes_per_step": n * elem_bytes}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_meld / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if keys_np.dtype == np.float32 else "u32",
+            "data": "synthetic",
+            "config": {"workload": desc, "n": n, "variant": "melded",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "flushed between steps (256 MiB write outside the timed events)",
+                       "hbm_passes": passes, "tile": tile},
+            "divergent": {"value": value_div, "ms_per_step": ms_div / args.steps},
+            "melded_over_divergent": value / value_div,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": f"{dom} pass",
+                         "peak_source": peak_src,
+                         "whole_sort_gbs": whole_sort_gbs,
+                         "whole_sort_frac": whole_sort_gbs / peak,
+                         "pass_ms": {k: statistics.mean(v) for k, v in per_kind.items()},
+                         "pass_share": {k: totals[k] / sum(totals.values()) for k in totals}},
+            "clocks": clk,
+            "gpu_launches": launches_meld + launches_div,
+        }
+        if e2e is not None:
+            line["e2e"] = e2e
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(keys_np, vals_np)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

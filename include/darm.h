@@ -1,0 +1,209 @@
+/*
+ * darm.h - C ABI of the GB300 bitonic compare-exchange library.
+ *
+ * The library sorts arrays that already live in device memory with the
+ * bitonic network of DARM's running example (Saumya, Sundararajah and
+ * Kulkarni, "DARM: Control-Flow Melding for SIMT Thread Divergence
+ * Reduction", Fig. 1 and Section III).  Every stage exists in two forms:
+ *
+ *   DARM_DIVERGENT  the direction test of Fig. 1 guards two full copies of
+ *                   the compare-exchange body (loads, compare, stores), one
+ *                   per direction, so threads whose blocks run in opposite
+ *                   directions diverge;
+ *   DARM_MELDED     the two copies melded as in Section IV-D/E and IV-G:
+ *                   loads and stores aligned into one copy, the two
+ *                   direction-specific compares kept as unaligned
+ *                   instructions, and a select on the direction choosing the
+ *                   swap condition.
+ *
+ * Both forms compute the same comparator network and give bit-identical
+ * results.  Conventions shared by every sorting entry point:
+ *
+ *   - Sorting is in place.  The caller owns `keys` and `vals`; both are
+ *     device pointers (e.g. from torch.empty(..., device="cuda")) aligned to
+ *     16 bytes.  `vals` may be NULL (keys only); otherwise it is a uint32
+ *     payload that travels with its key.
+ *   - n must be a power of two (Fig. 1's NUM); n = 0 and n = 1 are no-ops.
+ *     n is limited to 2^31.
+ *   - dir: DARM_ASC or DARM_DESC.  Descending flips every comparator of
+ *     Fig. 1 (the paper shows only the ascending network).
+ *   - A swap happens only on strict inequality, so the payload order among
+ *     equal keys is the one fixed by the network (not a stable order).
+ *   - Float keys are ordered by the IEEE-754 totalOrder of their bits
+ *     (-0.0 sorts just below +0.0); NaNs sort by bit pattern.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL is the legacy default stream).  Argument errors are returned
+ *     synchronously before anything is enqueued; launch failures return
+ *     DARM_ERR_CUDA.  Errors detected on the device (sentinel collisions,
+ *     bounded waits that ran out) are latched in a device status word that
+ *     darm_device_status() reads.
+ *   - darm_sort_init must be called first (per process; idempotent).  All
+ *     calls are safe from several host threads; kernels of different
+ *     streams may overlap.
+ */
+#ifndef DARM_H_
+#define DARM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DARM_OK = 0,
+  DARM_ERR_INVALID_ARG = 1,
+  DARM_ERR_NOT_POW2 = 2,
+  DARM_ERR_NOT_INIT = 3,
+  DARM_ERR_OOM = 4,
+  DARM_ERR_CUDA = 5,
+  DARM_ERR_BUDGET = 6,
+  DARM_ERR_TIMEOUT = 7,
+  DARM_ERR_SENTINEL_COLLISION = 8,
+  DARM_ERR_BUSY = 9,
+  DARM_ERR_NOT_FOUND = 10
+} darm_status;
+
+typedef enum { DARM_ASC = 0, DARM_DESC = 1 } darm_dir;
+
+typedef enum {
+  DARM_DIVERGENT = 0,
+  DARM_MELDED = 1,
+  DARM_AUTO = 2 /* the tuned choice (melded unless the tuner found better) */
+} darm_variant;
+
+typedef enum { DARM_U32 = 0, DARM_F32 = 1, DARM_U64 = 2 } darm_dtype;
+
+/* ---- context --------------------------------------------------------- */
+
+/* Select `device`, query its SM count, configure shared memory for every
+ * kernel and allocate the device status word plus `workspace_bytes` of
+ * scratch for host-buffer sorts (0 = grow on demand).  Idempotent: a second
+ * call with the same device returns DARM_OK. */
+int darm_sort_init(int device, size_t workspace_bytes);
+
+/* Release everything darm_sort_init and later calls allocated (plans,
+ * graphs, workspace, serving state).  The caller's buffers are untouched. */
+int darm_sort_finalize(void);
+
+/* Human-readable name of a darm_status value (static storage). */
+const char* darm_status_str(int status);
+
+/* Read and clear the device status word (synchronises the device).
+ * *status receives DARM_OK or the first device-detected error. */
+int darm_device_status(int* status);
+
+/* ---- whole-array sort (Fig. 1, one array of n = 2^m elements) ---------- */
+
+/* uint32 keys, optional uint32 payload. */
+int darm_bitonic_sort(uint32_t* keys, uint32_t* vals, size_t n, int dir,
+                      int variant, void* stream);
+
+/* float32 keys (totalOrder), optional uint32 payload. */
+int darm_bitonic_sort_f32(float* keys, uint32_t* vals, size_t n, int dir,
+                          int variant, void* stream);
+
+/* uint64 keys, optional uint32 payload. */
+int darm_bitonic_sort_u64(uint64_t* keys, uint32_t* vals, size_t n, int dir,
+                          int variant, void* stream);
+
+/* Same sort on HOST buffers: copies keys (and vals) into library-owned
+ * device memory, sorts, copies back and synchronises.  `dtype` is a
+ * darm_dtype.  Host buffers may be pageable; pinned memory is faster.
+ * Returns after the result is in the host buffers. */
+int darm_bitonic_sort_host(void* keys, uint32_t* vals, size_t n, int dtype,
+                           int dir, int variant);
+
+/* ---- batched segmented sort ------------------------------------------ */
+
+/* Sort num_segs independent segments in one batched launch sequence.
+ * Segment s occupies elements [seg_offsets[s], seg_offsets[s+1]) of keys
+ * and vals; its capacity (the difference) must be a power of two and the
+ * offsets a multiple of 4 elements.  Only the first seg_len[s] elements are
+ * real: the library writes the sentinel (UINT32_MAX for ascending, 0 for
+ * descending; payload 0xFFFFFFFF) beyond them and sorts the whole capacity,
+ * so the real keys end up first.  seg_offsets (uint64, num_segs + 1
+ * entries) and seg_len (uint32) are HOST arrays: the library builds a
+ * longest-first work list from them, uploads it once and replays the launch
+ * sequence as a CUDA graph on later calls with the same layout.
+ * seg_desc (HOST, uint8 per segment, nullable) overrides `dir` per segment.
+ * With a payload, a real key equal to the sentinel makes the result
+ * ambiguous; the kernel latches DARM_ERR_SENTINEL_COLLISION in the device
+ * status word (see darm_device_status) and still sorts. */
+int darm_segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* seg_offsets,
+                        const uint32_t* seg_len, uint32_t num_segs, int dir,
+                        int variant, const uint8_t* seg_desc, void* stream);
+
+/* ---- tuning ----------------------------------------------------------- */
+
+/* Time candidate tile sizes, elements per thread and per-stage variants for
+ * arrays of n elements of `dtype` (with payload if has_vals), keep the
+ * fastest as the plan DARM_AUTO uses, and append it to the text file
+ * db_path (NULL: keep in memory only).  Allocates and frees its own scratch;
+ * synchronises the device. */
+int darm_autotune(int dtype, size_t n, int has_vals, const char* db_path);
+
+/* Load plans previously written by darm_autotune. */
+int darm_load_tune_db(const char* db_path);
+
+/* ---- introspection ----------------------------------------------------- */
+
+/* Describe the launch sequence for a whole-array sort of n elements:
+ * passes = number of full read+write sweeps over the array in HBM,
+ * launches = kernel launches, tile = elements a tile pass keeps on chip. */
+int darm_plan_info(int dtype, size_t n, int has_vals, int variant,
+                   int* passes, int* launches, int* tile);
+
+/* Profiling run of a whole-array sort: the same launches as the plain call,
+ * with a CUDA event pair recorded on `stream` around each one.  Synchronises
+ * the stream, then writes for launch i < cap: ms[i] = its device time and
+ * kind[i] = 0 tile pass, 1 window pass, 2 merge pass; *count = launches.
+ * The keys are sorted exactly as by the plain call. */
+int darm_sort_profile(void* keys, uint32_t* vals, size_t n, int dtype, int dir, int variant,
+                      void* stream, float* ms, int* kind, int cap, int* count);
+
+/* Number of kernels this library has launched since darm_sort_init
+ * (graph replays count each kernel node). */
+uint64_t darm_launch_count(void);
+
+/* ---- serving: continuous batching of sort requests --------------------- */
+
+typedef struct {
+  size_t budget_bytes;  /* device memory all admitted jobs may hold */
+  int max_inflight;     /* admitted jobs at once */
+  int variant;          /* darm_variant for every job */
+  int num_streams;      /* streams the scheduler spreads batched launches over */
+} darm_serve_cfg;
+
+/* Start the scheduler thread.  It owns a device arena of budget_bytes. */
+int darm_sort_serve_start(const darm_serve_cfg* cfg);
+
+/* Queue a sort of n keys (device pointer `keys` of `dtype`, optional device
+ * payload `vals`) in direction `dir`.  n need not be a power of two: the
+ * job is padded to the next power of two with sentinels inside the arena
+ * and only the n real elements are written back.  The buffers must stay
+ * valid until the request is reported done.  Returns DARM_ERR_BUDGET if the
+ * job alone exceeds the budget. */
+int darm_sort_serve_submit(void* keys, uint32_t* vals, size_t n, int dtype,
+                           int dir, uint64_t* req_id);
+
+/* Non-blocking: *done = 1 once the result is in the caller's buffers. */
+int darm_sort_serve_poll(uint64_t req_id, int* done);
+
+/* Block until done or timeout_ms passes (DARM_ERR_TIMEOUT). */
+int darm_sort_serve_wait(uint64_t req_id, int timeout_ms);
+
+/* Latency percentiles (submit to completion) and throughput of all
+ * requests completed so far. */
+int darm_sort_serve_stats(double* p50_ms, double* p99_ms, double* keys_per_s,
+                          uint64_t* completed);
+
+/* Drain outstanding jobs, stop the scheduler and free the arena. */
+int darm_sort_serve_stop(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DARM_H_ */

@@ -1,0 +1,241 @@
+"""Python binding of the GB300 bitonic compare-exchange library (libdarm.so).
+
+Argument marshalling only: every step of a sort runs in the CUDA library
+behind the C ABI declared in include/darm.h.  PyTorch supplies device memory
+and streams.  There is no fallback: if the library is missing or fails to
+load, importing this package raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdarm.so")
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_NOT_POW2 = 2
+ERR_NOT_INIT = 3
+ERR_OOM = 4
+ERR_CUDA = 5
+ERR_BUDGET = 6
+ERR_TIMEOUT = 7
+ERR_SENTINEL_COLLISION = 8
+ERR_BUSY = 9
+ERR_NOT_FOUND = 10
+
+ASC, DESC = 0, 1
+DIVERGENT, MELDED, AUTO = 0, 1, 2
+U32, F32, U64 = 0, 1, 2
+
+_VARIANTS = {"divergent": DIVERGENT, "melded": MELDED, "auto": AUTO,
+             DIVERGENT: DIVERGENT, MELDED: MELDED, AUTO: AUTO}
+
+
+class DarmError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_str(status)}" if what else status_str(status))
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+        "(the library has no CPU fallback)")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+_vp, _u64, _i32, _sz = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t
+_sig = {
+    "darm_sort_init": ([_i32, _sz], _i32),
+    "darm_sort_finalize": ([], _i32),
+    "darm_status_str": ([_i32], ctypes.c_char_p),
+    "darm_device_status": ([ctypes.POINTER(_i32)], _i32),
+    "darm_bitonic_sort": ([_vp, _vp, _sz, _i32, _i32, _vp], _i32),
+    "darm_bitonic_sort_f32": ([_vp, _vp, _sz, _i32, _i32, _vp], _i32),
+    "darm_bitonic_sort_u64": ([_vp, _vp, _sz, _i32, _i32, _vp], _i32),
+    "darm_bitonic_sort_host": ([_vp, _vp, _sz, _i32, _i32, _i32], _i32),
+    "darm_segmented_sort": ([_vp, _vp, _vp, _vp, ctypes.c_uint32, _i32, _i32, _vp, _vp], _i32),
+    "darm_autotune": ([_i32, _sz, _i32, ctypes.c_char_p], _i32),
+    "darm_load_tune_db": ([ctypes.c_char_p], _i32),
+    "darm_plan_info": ([_i32, _sz, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                        ctypes.POINTER(_i32)], _i32),
+    "darm_launch_count": ([], _u64),
+    "darm_sort_profile": ([_vp, _vp, _sz, _i32, _i32, _i32, _vp, ctypes.POINTER(ctypes.c_float),
+                           ctypes.POINTER(_i32), _i32, ctypes.POINTER(_i32)], _i32),
+    "darm_sort_serve_start": ([_vp], _i32),
+    "darm_sort_serve_submit": ([_vp, _vp, _sz, _i32, _i32, ctypes.POINTER(_u64)], _i32),
+    "darm_sort_serve_poll": ([_u64, ctypes.POINTER(_i32)], _i32),
+    "darm_sort_serve_wait": ([_u64, _i32], _i32),
+    "darm_sort_serve_stats": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u64)], _i32),
+    "darm_sort_serve_stop": ([], _i32),
+}
+for _name, (_args, _res) in _sig.items():
+    _fn = getattr(lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _res
+
+EXPORTED = tuple(_sig)
+
+
+class ServeCfg(ctypes.Structure):
+    _fields_ = [("budget_bytes", _sz), ("max_inflight", _i32), ("variant", _i32),
+                ("num_streams", _i32)]
+
+
+def status_str(status: int) -> str:
+    return lib.darm_status_str(int(status)).decode()
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != OK:
+        raise DarmError(rc, what)
+
+
+def _variant(v) -> int:
+    try:
+        return _VARIANTS[v]
+    except KeyError:
+        raise ValueError(f"unknown variant {v!r}") from None
+
+
+def init(device: int = 0, workspace_bytes: int = 0) -> None:
+    _check(lib.darm_sort_init(int(device), int(workspace_bytes)), "darm_sort_init")
+
+
+def finalize() -> None:
+    _check(lib.darm_sort_finalize(), "darm_sort_finalize")
+
+
+def device_status() -> int:
+    st = ctypes.c_int(0)
+    _check(lib.darm_device_status(ctypes.byref(st)), "darm_device_status")
+    return st.value
+
+
+def launch_count() -> int:
+    return int(lib.darm_launch_count())
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def sort(keys, vals=None, descending: bool = False, variant="melded", stream=None) -> None:
+    """Sort a contiguous CUDA tensor of uint32, float32 or uint64 keys in place
+    (payload `vals`, a uint32 tensor, travels with its key)."""
+    import torch
+    if not keys.is_cuda or not keys.is_contiguous() or keys.dim() != 1:
+        raise ValueError("keys must be a contiguous 1-D CUDA tensor")
+    vp = None
+    if vals is not None:
+        if vals.dtype != torch.uint32 or vals.shape != keys.shape or not vals.is_contiguous():
+            raise ValueError("vals must be a contiguous uint32 CUDA tensor shaped like keys")
+        vp = ctypes.c_void_p(vals.data_ptr())
+    kp = ctypes.c_void_p(keys.data_ptr())
+    n = keys.numel()
+    d = DESC if descending else ASC
+    v = _variant(variant)
+    s = _stream_handle(stream)
+    if keys.dtype == torch.uint32:
+        rc = lib.darm_bitonic_sort(kp, vp, n, d, v, s)
+    elif keys.dtype == torch.float32:
+        rc = lib.darm_bitonic_sort_f32(kp, vp, n, d, v, s)
+    elif keys.dtype == torch.uint64:
+        rc = lib.darm_bitonic_sort_u64(kp, vp, n, d, v, s)
+    else:
+        raise ValueError(f"unsupported key dtype {keys.dtype}")
+    _check(rc, "darm_bitonic_sort")
+
+
+def sort_host(keys, vals=None, descending: bool = False, variant="melded") -> None:
+    """Sort numpy arrays (host memory) in place through the library: the
+    library copies them to the device, sorts and copies them back."""
+    import numpy as np
+    if not keys.flags.c_contiguous:
+        raise ValueError("keys must be C-contiguous")
+    dt = {np.dtype(np.uint32): U32, np.dtype(np.float32): F32,
+          np.dtype(np.uint64): U64}.get(keys.dtype)
+    if dt is None:
+        raise ValueError(f"unsupported key dtype {keys.dtype}")
+    vp = None
+    if vals is not None:
+        if vals.dtype != np.uint32 or vals.shape != keys.shape or not vals.flags.c_contiguous:
+            raise ValueError("vals must be a C-contiguous uint32 array shaped like keys")
+        vp = vals.ctypes.data_as(ctypes.c_void_p)
+    rc = lib.darm_bitonic_sort_host(keys.ctypes.data_as(ctypes.c_void_p), vp, keys.size, dt,
+                                    DESC if descending else ASC, _variant(variant))
+    _check(rc, "darm_bitonic_sort_host")
+
+
+def segmented_sort(keys, vals, offsets, lengths, descending: bool = False, variant="melded",
+                   seg_desc=None, stream=None) -> None:
+    """Sort independent power-of-two segments of a uint32 CUDA tensor in place.
+
+    offsets (num_segments + 1, uint64) and lengths (uint32) are host numpy
+    arrays; seg_desc (uint8 per segment) optionally overrides the direction.
+    """
+    import numpy as np
+    import torch
+    if keys.dtype != torch.uint32 or not keys.is_cuda or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous uint32 CUDA tensor")
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    ln = np.ascontiguousarray(lengths, dtype=np.uint32)
+    if off.size != ln.size + 1:
+        raise ValueError("offsets must have num_segments + 1 entries")
+    dp = None
+    if seg_desc is not None:
+        dd = np.ascontiguousarray(seg_desc, dtype=np.uint8)
+        dp = dd.ctypes.data_as(ctypes.c_void_p)
+    vp = None if vals is None else ctypes.c_void_p(vals.data_ptr())
+    rc = lib.darm_segmented_sort(ctypes.c_void_p(keys.data_ptr()), vp,
+                                 off.ctypes.data_as(ctypes.c_void_p),
+                                 ln.ctypes.data_as(ctypes.c_void_p), ln.size,
+                                 DESC if descending else ASC, _variant(variant), dp,
+                                 _stream_handle(stream))
+    _check(rc, "darm_segmented_sort")
+
+
+def plan_info(dtype: int, n: int, has_vals: bool, variant="melded"):
+    """(passes, launches, tile) of the whole-array plan for n elements."""
+    p, l, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib.darm_plan_info(int(dtype), int(n), int(bool(has_vals)), _variant(variant),
+                              ctypes.byref(p), ctypes.byref(l), ctypes.byref(t)),
+           "darm_plan_info")
+    return p.value, l.value, t.value
+
+
+PASS_NAMES = ("tile", "window", "merge")
+
+
+def sort_profile(keys, vals=None, descending: bool = False, variant="melded", stream=None):
+    """Sort in place like sort(), timing each kernel launch with CUDA events
+    on the launching stream.  Returns a list of (pass name, milliseconds)."""
+    import torch
+    dt = {torch.uint32: U32, torch.float32: F32, torch.uint64: U64}.get(keys.dtype)
+    if dt is None or not keys.is_cuda or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous uint32/float32/uint64 CUDA tensor")
+    cap = 256
+    ms = (ctypes.c_float * cap)()
+    kinds = (_i32 * cap)()
+    cnt = _i32(0)
+    vp = None if vals is None else ctypes.c_void_p(vals.data_ptr())
+    _check(lib.darm_sort_profile(ctypes.c_void_p(keys.data_ptr()), vp, keys.numel(), dt,
+                                 DESC if descending else ASC, _variant(variant),
+                                 _stream_handle(stream), ms, kinds, cap, ctypes.byref(cnt)),
+           "darm_sort_profile")
+    return [(PASS_NAMES[kinds[i]], float(ms[i])) for i in range(min(cnt.value, cap))]
+
+
+def autotune(dtype: int, n: int, has_vals: bool, db_path: str | None = None) -> None:
+    _check(lib.darm_autotune(int(dtype), int(n), int(bool(has_vals)),
+                             None if db_path is None else db_path.encode()), "darm_autotune")
+
+
+def load_tune_db(db_path: str) -> None:
+    _check(lib.darm_load_tune_db(db_path.encode()), "darm_load_tune_db")

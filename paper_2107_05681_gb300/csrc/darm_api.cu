@@ -1,0 +1,298 @@
+// darm_api.cu - the C ABI (include/darm.h): context, whole-array sorts,
+// host-buffer sorts, plan introspection and the launch path shared by the
+// segmented sort and the serving loop.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "darm.h"
+#include "darm_internal.h"
+#include "kernel_table.h"
+#include "plan.h"
+
+namespace darm {
+
+Context g_ctx;
+
+const void* kernel_fn(KeyKind kk, bool has_vals, int loge, int variant) {
+  KernelEntry e = (kk == KEY_U32) ? kernel_u32(has_vals, loge, variant)
+                                  : kernel_u64(has_vals, loge, variant);
+  return e.fn;
+}
+
+int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_t* vals,
+                cudaStream_t stream) {
+  const bool has_vals = vals != nullptr;
+  for (const Launch& L : plan) {
+    PassParams P = L.P;
+    P.keys = keys;
+    P.vals = vals;
+    P.status = g_ctx.d_status;
+    const void* fn = kernel_fn(kk, has_vals, L.loge, L.variant);
+    if (!fn) return DARM_ERR_INVALID_ARG;
+    void* args[] = {&P};
+    cudaError_t err = cudaLaunchKernel(fn, dim3(L.grid), dim3(L.threads), args, L.smem, stream);
+    if (err != cudaSuccess) {
+      fprintf(stderr, "darm: launch failed: %s\n", cudaGetErrorString(err));
+      return DARM_ERR_CUDA;
+    }
+    g_ctx.launches.fetch_add(1, std::memory_order_relaxed);
+  }
+  return DARM_OK;
+}
+
+static int log2_exact(size_t n) {
+  int m = 0;
+  while ((size_t(1) << m) < n) ++m;
+  return m;
+}
+
+Tuning tuning_for(KeyKind kk, bool has_vals, int m) {
+  std::lock_guard<std::mutex> lk(g_ctx.mu);
+  auto it = g_ctx.tuned.find(std::make_tuple(int(kk), int(has_vals), m));
+  if (it != g_ctx.tuned.end()) return it->second;
+  return default_tuning(kk, has_vals);
+}
+
+const std::vector<Launch>* cached_plan(KeyKind kk, bool has_vals, int m, int variant,
+                                       uint32_t map_in, uint32_t map_out) {
+  const Tuning tn = tuning_for(kk, has_vals, m);
+  PlanKey key{int(kk), int(has_vals), m, variant, map_in, map_out, tn.t, tn.e1, tn.e2, tn.c2,
+              tn.var[0] * 4 + tn.var[1] * 2 + tn.var[2]};
+  std::lock_guard<std::mutex> lk(g_ctx.mu);
+  auto it = g_ctx.plans.find(key);
+  if (it != g_ctx.plans.end()) return &it->second;
+  std::vector<Launch> plan;
+  if (!plan_array(plan, kk, has_vals, m, tn, variant, map_in, map_out, g_ctx.smem_limit))
+    return nullptr;
+  auto res = g_ctx.plans.emplace(key, std::move(plan));
+  return &res.first->second;
+}
+
+int check_common(const void* keys, const void* vals, size_t n, int dir, int variant) {
+  if (!g_ctx.inited) return DARM_ERR_NOT_INIT;
+  if (dir != DARM_ASC && dir != DARM_DESC) return DARM_ERR_INVALID_ARG;
+  if (variant < DARM_DIVERGENT || variant > DARM_AUTO) return DARM_ERR_INVALID_ARG;
+  if (n <= 1) return DARM_OK;
+  if ((n & (n - 1)) != 0) return DARM_ERR_NOT_POW2;
+  if (n > (size_t(1) << 31)) return DARM_ERR_INVALID_ARG;
+  if (keys == nullptr) return DARM_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(keys) & 15u) != 0) return DARM_ERR_INVALID_ARG;
+  if (vals != nullptr && (reinterpret_cast<uintptr_t>(vals) & 15u) != 0) return DARM_ERR_INVALID_ARG;
+  return -1;  // proceed
+}
+
+int sort_device(KeyKind kk, bool f32, void* keys, uint32_t* vals, size_t n, int dir, int variant,
+                cudaStream_t stream) {
+  const int rc = check_common(keys, vals, n, dir, variant);
+  if (rc >= 0) return rc;
+  const int m = log2_exact(n);
+  const uint32_t map = (f32 ? kMapF32 : 0u) | (dir == DARM_DESC ? kMapComplement : 0u);
+  const std::vector<Launch>* plan = cached_plan(kk, vals != nullptr, m, variant, map, map);
+  if (!plan) return DARM_ERR_INVALID_ARG;
+  return launch_plan(*plan, kk, keys, vals, stream);
+}
+
+static void set_smem_attr(const void* fn, void* ctx) {
+  const int bytes = *static_cast<int*>(ctx);
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+}  // namespace darm
+
+using namespace darm;
+
+extern "C" {
+
+int darm_sort_init(int device, size_t workspace_bytes) {
+  std::lock_guard<std::mutex> lk(g_ctx.mu);
+  if (g_ctx.inited) return device == g_ctx.device ? DARM_OK : DARM_ERR_BUSY;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return DARM_ERR_INVALID_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return DARM_ERR_CUDA;
+  int sms = 0, optin = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  g_ctx.device = device;
+  g_ctx.sms = sms;
+  g_ctx.smem_limit = size_t(optin);
+  for_each_kernel_u32(set_smem_attr, &optin);
+  for_each_kernel_u64(set_smem_attr, &optin);
+  if (cudaMalloc(&g_ctx.d_status, sizeof(int)) != cudaSuccess) return DARM_ERR_OOM;
+  if (cudaMemset(g_ctx.d_status, 0, sizeof(int)) != cudaSuccess) return DARM_ERR_CUDA;
+  if (cudaStreamCreateWithFlags(&g_ctx.host_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return DARM_ERR_CUDA;
+  if (workspace_bytes) {
+    if (cudaMalloc(&g_ctx.ws, workspace_bytes) != cudaSuccess) return DARM_ERR_OOM;
+    g_ctx.ws_bytes = workspace_bytes;
+  }
+  if (cudaGetLastError() != cudaSuccess) return DARM_ERR_CUDA;
+  g_ctx.launches.store(0);
+  g_ctx.inited = true;
+  return DARM_OK;
+}
+
+int darm_sort_finalize(void) {
+  darm_sort_serve_stop();
+  segmented_release_all();
+  std::lock_guard<std::mutex> lk(g_ctx.mu);
+  if (!g_ctx.inited) return DARM_OK;
+  cudaDeviceSynchronize();
+  if (g_ctx.ws) cudaFree(g_ctx.ws);
+  if (g_ctx.d_status) cudaFree(g_ctx.d_status);
+  if (g_ctx.host_stream) cudaStreamDestroy(g_ctx.host_stream);
+  g_ctx.ws = nullptr;
+  g_ctx.ws_bytes = 0;
+  g_ctx.d_status = nullptr;
+  g_ctx.host_stream = nullptr;
+  g_ctx.plans.clear();
+  g_ctx.inited = false;
+  return DARM_OK;
+}
+
+const char* darm_status_str(int status) {
+  switch (status) {
+    case DARM_OK: return "DARM_OK";
+    case DARM_ERR_INVALID_ARG: return "DARM_ERR_INVALID_ARG";
+    case DARM_ERR_NOT_POW2: return "DARM_ERR_NOT_POW2";
+    case DARM_ERR_NOT_INIT: return "DARM_ERR_NOT_INIT";
+    case DARM_ERR_OOM: return "DARM_ERR_OOM";
+    case DARM_ERR_CUDA: return "DARM_ERR_CUDA";
+    case DARM_ERR_BUDGET: return "DARM_ERR_BUDGET";
+    case DARM_ERR_TIMEOUT: return "DARM_ERR_TIMEOUT";
+    case DARM_ERR_SENTINEL_COLLISION: return "DARM_ERR_SENTINEL_COLLISION";
+    case DARM_ERR_BUSY: return "DARM_ERR_BUSY";
+    case DARM_ERR_NOT_FOUND: return "DARM_ERR_NOT_FOUND";
+    default: return "DARM_ERR_UNKNOWN";
+  }
+}
+
+int darm_device_status(int* status) {
+  if (!g_ctx.inited) return DARM_ERR_NOT_INIT;
+  if (!status) return DARM_ERR_INVALID_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return DARM_ERR_CUDA;
+  int h = 0;
+  if (cudaMemcpy(&h, g_ctx.d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DARM_ERR_CUDA;
+  if (cudaMemset(g_ctx.d_status, 0, sizeof(int)) != cudaSuccess) return DARM_ERR_CUDA;
+  *status = h;
+  return DARM_OK;
+}
+
+int darm_bitonic_sort(uint32_t* keys, uint32_t* vals, size_t n, int dir, int variant,
+                      void* stream) {
+  return sort_device(KEY_U32, false, keys, vals, n, dir, variant,
+                     static_cast<cudaStream_t>(stream));
+}
+
+int darm_bitonic_sort_f32(float* keys, uint32_t* vals, size_t n, int dir, int variant,
+                          void* stream) {
+  return sort_device(KEY_U32, true, keys, vals, n, dir, variant,
+                     static_cast<cudaStream_t>(stream));
+}
+
+int darm_bitonic_sort_u64(uint64_t* keys, uint32_t* vals, size_t n, int dir, int variant,
+                          void* stream) {
+  return sort_device(KEY_U64, false, keys, vals, n, dir, variant,
+                     static_cast<cudaStream_t>(stream));
+}
+
+int darm_bitonic_sort_host(void* keys, uint32_t* vals, size_t n, int dtype, int dir,
+                           int variant) {
+  if (!g_ctx.inited) return DARM_ERR_NOT_INIT;
+  if (dtype < DARM_U32 || dtype > DARM_U64) return DARM_ERR_INVALID_ARG;
+  if (n <= 1) return DARM_OK;
+  if ((n & (n - 1)) != 0) return DARM_ERR_NOT_POW2;
+  if (!keys) return DARM_ERR_INVALID_ARG;
+  const size_t kbytes = n * (dtype == DARM_U64 ? 8 : 4);
+  const size_t vbytes = vals ? n * 4 : 0;
+  const size_t need = kbytes + ((vbytes + 255) & ~size_t(255)) + 256;
+  std::lock_guard<std::mutex> lk(g_ctx.host_mu);
+  if (g_ctx.ws_bytes < need) {
+    if (g_ctx.ws) cudaFree(g_ctx.ws);
+    g_ctx.ws = nullptr;
+    g_ctx.ws_bytes = 0;
+    if (cudaMalloc(&g_ctx.ws, need) != cudaSuccess) return DARM_ERR_OOM;
+    g_ctx.ws_bytes = need;
+  }
+  char* base = static_cast<char*>(g_ctx.ws);
+  void* dk = base;
+  uint32_t* dv = vals ? reinterpret_cast<uint32_t*>(base + ((kbytes + 255) & ~size_t(255))) : nullptr;
+  cudaStream_t s = g_ctx.host_stream;
+  if (cudaMemcpyAsync(dk, keys, kbytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return DARM_ERR_CUDA;
+  if (vals && cudaMemcpyAsync(dv, vals, vbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return DARM_ERR_CUDA;
+  int rc;
+  if (dtype == DARM_U64)
+    rc = sort_device(KEY_U64, false, dk, dv, n, dir, variant, s);
+  else
+    rc = sort_device(KEY_U32, dtype == DARM_F32, dk, dv, n, dir, variant, s);
+  if (rc != DARM_OK) return rc;
+  if (cudaMemcpyAsync(keys, dk, kbytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DARM_ERR_CUDA;
+  if (vals && cudaMemcpyAsync(vals, dv, vbytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return DARM_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return DARM_ERR_CUDA;
+  return DARM_OK;
+}
+
+int darm_plan_info(int dtype, size_t n, int has_vals, int variant, int* passes, int* launches,
+                   int* tile) {
+  if (!g_ctx.inited) return DARM_ERR_NOT_INIT;
+  if (dtype < DARM_U32 || dtype > DARM_U64) return DARM_ERR_INVALID_ARG;
+  if (n < 2 || (n & (n - 1)) != 0) return DARM_ERR_NOT_POW2;
+  const KeyKind kk = dtype == DARM_U64 ? KEY_U64 : KEY_U32;
+  const int m = log2_exact(n);
+  const std::vector<Launch>* plan = cached_plan(kk, has_vals != 0, m, variant, 0, 0);
+  if (!plan) return DARM_ERR_INVALID_ARG;
+  if (passes) *passes = int(plan->size());
+  if (launches) *launches = int(plan->size());
+  if (tile) *tile = plan->empty() ? 0 : int(1u << plan->front().P.b);
+  return DARM_OK;
+}
+
+uint64_t darm_launch_count(void) { return g_ctx.launches.load(); }
+
+int darm_sort_profile(void* keys, uint32_t* vals, size_t n, int dtype, int dir, int variant,
+                      void* stream, float* ms, int* kind, int cap, int* count) {
+  if (dtype < DARM_U32 || dtype > DARM_U64) return DARM_ERR_INVALID_ARG;
+  const int rc0 = check_common(keys, vals, n, dir, variant);
+  if (rc0 >= 0) return rc0;
+  const KeyKind kk = dtype == DARM_U64 ? KEY_U64 : KEY_U32;
+  const int m = log2_exact(n);
+  const uint32_t map = (dtype == DARM_F32 ? kMapF32 : 0u) | (dir == DARM_DESC ? kMapComplement : 0u);
+  const std::vector<Launch>* plan = cached_plan(kk, vals != nullptr, m, variant, map, map);
+  if (!plan) return DARM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t L = plan->size();
+  std::vector<cudaEvent_t> ev(L + 1);
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return DARM_ERR_CUDA;
+  int rc = DARM_OK;
+  cudaEventRecord(ev[0], s);
+  for (size_t i = 0; i < L && rc == DARM_OK; ++i) {
+    std::vector<Launch> one(1, (*plan)[i]);
+    rc = launch_plan(one, kk, keys, vals, s);
+    cudaEventRecord(ev[i + 1], s);
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) rc = DARM_ERR_CUDA;
+  for (size_t i = 0; i < L && rc == DARM_OK; ++i) {
+    if (int(i) < cap) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+      if (ms) ms[i] = t;
+      if (kind) kind[i] = int((*plan)[i].kind);
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (count) *count = int(L);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,48 @@
+// darm_internal.h - state and helpers shared by the library's translation
+// units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "plan.h"
+
+namespace darm {
+
+// Everything that identifies a compiled whole-array plan.
+using PlanKey = std::tuple<int, int, int, int, uint32_t, uint32_t, int, int, int, int, int>;
+
+struct Context {
+  bool inited = false;
+  int device = -1;
+  int sms = 0;
+  size_t smem_limit = 0;
+  int* d_status = nullptr;           // device status word
+  cudaStream_t host_stream = nullptr;  // stream of host-buffer sorts
+  void* ws = nullptr;                // workspace of host-buffer sorts
+  size_t ws_bytes = 0;
+  std::mutex mu;       // plans, tuning table, init/finalize
+  std::mutex host_mu;  // host-buffer workspace
+  std::atomic<uint64_t> launches{0};
+  std::map<std::tuple<int, int, int>, Tuning> tuned;  // (key kind, has vals, log2 n)
+  std::map<PlanKey, std::vector<Launch>> plans;
+};
+
+extern Context g_ctx;
+
+const void* kernel_fn(KeyKind kk, bool has_vals, int loge, int variant);
+int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_t* vals,
+                cudaStream_t stream);
+Tuning tuning_for(KeyKind kk, bool has_vals, int m);
+const std::vector<Launch>* cached_plan(KeyKind kk, bool has_vals, int m, int variant,
+                                       uint32_t map_in, uint32_t map_out);
+int sort_device(KeyKind kk, bool f32, void* keys, uint32_t* vals, size_t n, int dir, int variant,
+                cudaStream_t stream);
+void segmented_release_all();
+
+}  // namespace darm

@@ -1,0 +1,24 @@
+// kernel_table.h - host-side lookup of the compiled pass-kernel
+// instantiations (one per key type, payload flag, elements per thread and
+// variant).
+#pragma once
+
+#include <cstdint>
+
+namespace darm {
+
+struct KernelEntry {
+  const void* fn;   // __global__ function address, or nullptr if not built
+  int max_threads;  // block size the instantiation was compiled for
+};
+
+// loge: log2 elements per thread (1..5); var: 0 divergent, 1 melded.
+KernelEntry kernel_u32(bool has_vals, int loge, int var);
+KernelEntry kernel_u64(bool has_vals, int loge, int var);
+
+// Call fn(kernel address, ctx) for every instantiation (used to configure
+// shared-memory limits once per device).
+void for_each_kernel_u32(void (*fn)(const void*, void*), void* ctx);
+void for_each_kernel_u64(void (*fn)(const void*, void*), void* ctx);
+
+}  // namespace darm

@@ -1,0 +1,226 @@
+// plan.cu - host planner for the bitonic network's passes (see plan.h).
+#include <algorithm>
+#include <cstdio>
+#include <sstream>
+
+#include "kernel_table.h"
+#include "plan.h"
+
+namespace darm {
+
+static int max_threads(KeyKind kk, bool has_vals, int loge) {
+  KernelEntry e = (kk == KEY_U32) ? kernel_u32(has_vals, loge, 1) : kernel_u64(has_vals, loge, 1);
+  return e.fn ? e.max_threads : 0;
+}
+
+Tuning default_tuning(KeyKind kk, bool has_vals) {
+  const int words = (kk == KEY_U32 ? 1 : 2) + (has_vals ? 1 : 0);
+  Tuning tn;
+  if (words == 1) {
+    tn.t = 14;  // 16 Ki uint32 keys = 64 KiB of shared memory per tile
+    tn.e1 = 4;
+    tn.e2 = 5;
+    tn.c2 = 8;
+  } else if (words == 2) {
+    tn.t = 13;  // 8 Ki elements of 8 bytes = 64 KiB
+    tn.e1 = 4;
+    tn.e2 = 4;
+    tn.c2 = 8;
+  } else {
+    tn.t = 12;  // 4 Ki elements of 12 bytes = 48 KiB
+    tn.e1 = 3;
+    tn.e2 = 3;
+    tn.c2 = 8;
+  }
+  tn.var[0] = tn.var[1] = tn.var[2] = kMelded;
+  return tn;
+}
+
+static int count_tile_rounds(int t, int e) {
+  int r = 1;
+  for (int p = e + 1; p <= t; ++p) r += (p + e - 1) / e;
+  return r;
+}
+
+bool fit_tuning(Tuning& tn, KeyKind kk, bool has_vals, int m, size_t smem_limit) {
+  if (m < 1) return false;
+  tn.e1 = std::max(1, std::min(tn.e1, 5));
+  tn.e2 = std::max(1, std::min(tn.e2, 5));
+  tn.t = std::min(tn.t, m);
+  // shared memory: one tile of keys + payload
+  while (tn.t > 1 && (size_t(elem_bytes(kk, has_vals)) << tn.t) > smem_limit) --tn.t;
+  tn.e1 = std::min(tn.e1, tn.t);
+  if (tn.t >= 2) tn.e1 = std::max(tn.e1, 2);
+  // block size of tile passes must fit the instantiation
+  while ((1 << (tn.t - tn.e1)) > max_threads(kk, has_vals, tn.e1)) {
+    if (tn.e1 < 5) {
+      ++tn.e1;
+    } else {
+      --tn.t;
+    }
+  }
+  while (count_tile_rounds(tn.t, tn.e1) > kMaxRounds) ++tn.e1;
+  if (tn.e1 > 5 || tn.e1 > tn.t) return false;
+  // window passes: threads cover low bits, window of e2 bits
+  tn.c2 = std::max(0, std::min(tn.c2, 10));
+  while ((1 << tn.c2) > max_threads(kk, has_vals, tn.e2)) --tn.c2;
+  return true;
+}
+
+std::vector<Round> tile_rounds(int t, int e) {
+  std::vector<Round> rs;
+  Round a{};
+  a.kind = RK_PHASE_A;
+  a.p = uint8_t(e);
+  a.a = 0;
+  a.cnt = uint8_t(e);
+  a.src = LOC_GLOBAL;
+  a.dst = (t == e) ? LOC_GLOBAL : LOC_SMEM;
+  rs.push_back(a);
+  for (int p = e + 1; p <= t; ++p) {
+    const int nw = (p + e - 1) / e;
+    for (int i = nw - 1; i >= 0; --i) {
+      const int lo = i * e;
+      const int hi = std::min((i + 1) * e, p) - 1;
+      Round r{};
+      r.kind = RK_WINDOW;
+      r.p = uint8_t(p);
+      r.a = uint8_t(hi - e + 1);
+      r.cnt = uint8_t(hi - lo + 1);
+      r.src = LOC_SMEM;
+      r.dst = LOC_SMEM;
+      rs.push_back(r);
+    }
+  }
+  rs.back().dst = LOC_GLOBAL;
+  return rs;
+}
+
+std::vector<Round> merge_rounds(int t, int e, int p) {
+  std::vector<Round> rs;
+  const int nw = (t + e - 1) / e;
+  for (int i = nw - 1; i >= 0; --i) {
+    const int lo = i * e;
+    const int hi = std::min((i + 1) * e, t) - 1;
+    Round r{};
+    r.kind = RK_WINDOW;
+    r.p = uint8_t(p);
+    r.a = uint8_t(hi - e + 1);
+    r.cnt = uint8_t(hi - lo + 1);
+    r.src = LOC_SMEM;
+    r.dst = LOC_SMEM;
+    rs.push_back(r);
+  }
+  rs.front().src = LOC_GLOBAL;
+  rs.back().dst = LOC_GLOBAL;
+  return rs;
+}
+
+static void set_rounds(PassParams& P, const std::vector<Round>& rs) {
+  P.nrounds = uint32_t(rs.size());
+  for (size_t i = 0; i < rs.size(); ++i) P.rounds[i] = rs[i];
+}
+
+static bool uses_smem(const std::vector<Round>& rs) {
+  for (const Round& r : rs)
+    if (r.src == LOC_SMEM || r.dst == LOC_SMEM) return true;
+  return false;
+}
+
+static int pick_var(int variant, const Tuning& tn, PassKind k) {
+  return (variant == 0 || variant == 1) ? variant : tn.var[k];
+}
+
+bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, const Tuning& tn0,
+                int variant, uint32_t map_in, uint32_t map_out, size_t smem_limit) {
+  out.clear();
+  Tuning tn = tn0;
+  if (!fit_tuning(tn, kk, has_vals, m, smem_limit)) return false;
+  const int t = tn.t, e1 = tn.e1, e2 = tn.e2;
+  const size_t tile_smem = size_t(elem_bytes(kk, has_vals)) << t;
+
+  // tile pass
+  {
+    Launch L{};
+    L.kind = PASS_TILE;
+    L.loge = e1;
+    L.variant = pick_var(variant, tn, PASS_TILE);
+    L.grid = uint32_t(1u << (m - t));
+    L.threads = 1u << (t - e1);
+    std::vector<Round> rs = tile_rounds(t, e1);
+    L.smem = uses_smem(rs) ? tile_smem : 0;
+    L.P.b = uint32_t(t);
+    L.P.c = uint32_t(t);
+    L.P.w0 = uint32_t(t);
+    L.P.s = 0;
+    L.P.log2cap = uint32_t(m);
+    L.P.map_in = map_in;
+    L.P.map_out = (m == t) ? map_out : 0u;
+    set_rounds(L.P, rs);
+    out.push_back(L);
+  }
+  for (int p = t + 1; p <= m; ++p) {
+    // window passes over layer bits t .. p-1, highest window first
+    const int nbits = p - t;
+    const int nw = (nbits + e2 - 1) / e2;
+    for (int i = nw - 1; i >= 0; --i) {
+      const int lo = t + i * e2;
+      const int hi = std::min(t + (i + 1) * e2, p) - 1;
+      const int w0 = hi - e2 + 1;
+      const int c = std::min(tn.c2, w0);
+      Launch L{};
+      L.kind = PASS_WINDOW;
+      L.loge = e2;
+      L.variant = pick_var(variant, tn, PASS_WINDOW);
+      L.threads = 1u << c;
+      L.grid = uint32_t(1u << (m - c - e2));
+      L.smem = 0;
+      L.P.b = uint32_t(c + e2);
+      L.P.c = uint32_t(c);
+      L.P.w0 = uint32_t(w0);
+      L.P.s = uint32_t(e2);
+      L.P.log2cap = uint32_t(m);
+      Round r{};
+      r.kind = RK_WINDOW;
+      r.p = uint8_t(p);
+      r.a = uint8_t(c);
+      r.cnt = uint8_t(hi - lo + 1);
+      r.src = LOC_GLOBAL;
+      r.dst = LOC_GLOBAL;
+      set_rounds(L.P, std::vector<Round>{r});
+      out.push_back(L);
+    }
+    // merge pass: layers t-1 .. 0 inside each tile
+    Launch L{};
+    L.kind = PASS_MERGE;
+    L.loge = e1;
+    L.variant = pick_var(variant, tn, PASS_MERGE);
+    L.grid = uint32_t(1u << (m - t));
+    L.threads = 1u << (t - e1);
+    std::vector<Round> rs = merge_rounds(t, e1, p);
+    L.smem = uses_smem(rs) ? tile_smem : 0;
+    L.P.b = uint32_t(t);
+    L.P.c = uint32_t(t);
+    L.P.w0 = uint32_t(t);
+    L.P.s = 0;
+    L.P.log2cap = uint32_t(m);
+    L.P.map_in = 0;
+    L.P.map_out = (p == m) ? map_out : 0u;
+    set_rounds(L.P, rs);
+    out.push_back(L);
+  }
+  return true;
+}
+
+std::string describe(const std::vector<Launch>& plan) {
+  std::ostringstream os;
+  static const char* names[] = {"tile", "window", "merge"};
+  for (const Launch& L : plan) {
+    os << names[L.kind] << " E=" << (1 << L.loge) << " var=" << L.variant << " grid=" << L.grid
+       << " threads=" << L.threads << " smem=" << L.smem << " b=" << L.P.b << " c=" << L.P.c
+       << " w0=" << L.P.w0 << " rounds=" << L.P.nrounds << "\n";
+  }
+  return os.str();
+}
+
+}  // namespace darm

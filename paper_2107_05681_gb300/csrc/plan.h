@@ -1,0 +1,71 @@
+// plan.h - host-side planner: turns a sort request into a list of pass
+// launches of the round kernel (pass_kernel.cuh).
+//
+// Schedule for one array of n = 2^m elements and a tile of T = 2^t
+// elements (t <= m):
+//   tile pass     stages k = 2 .. T inside each tile (Phase A in registers
+//                 for k <= E, then register windows through shared memory);
+//   for every stage k = 2T .. n (p = log2 k):
+//     window passes   layers j >= T, LOGE2 of them per pass, straight from
+//                     HBM to registers and back (the direction is uniform per
+//                     block because bit k lies above the window);
+//     merge pass      layers j < T inside each tile.
+// Every pass reads and writes the array once, so the HBM traffic of a sort
+// is 2 * n * (bytes per element) * passes.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "pass_kernel.cuh"
+
+namespace darm {
+
+enum KeyKind { KEY_U32 = 0, KEY_U64 = 1 };
+enum PassKind { PASS_TILE = 0, PASS_WINDOW = 1, PASS_MERGE = 2 };
+
+struct Tuning {
+  int t;      // log2 tile elements (tile and merge passes)
+  int e1;     // log2 elements per thread in tile and merge passes
+  int e2;     // log2 elements per thread in window passes
+  int c2;     // log2 threads per block in window passes
+  int var[3]; // variant per pass kind (used when DARM_AUTO is requested)
+};
+
+struct Launch {
+  PassKind kind;
+  int loge;
+  int variant;
+  uint32_t grid;
+  uint32_t threads;
+  size_t smem;
+  PassParams P;
+};
+
+// Bytes one element occupies (key + optional payload).
+inline int elem_bytes(KeyKind kk, bool has_vals) {
+  return (kk == KEY_U32 ? 4 : 8) + (has_vals ? 4 : 0);
+}
+
+Tuning default_tuning(KeyKind kk, bool has_vals);
+
+// Clamp a tuning to what the compiled kernels and the device allow for an
+// array of 2^m elements.  Returns false if no valid plan exists.
+bool fit_tuning(Tuning& tn, KeyKind kk, bool has_vals, int m, size_t smem_limit);
+
+// Rounds of a tile pass (stages 2 .. 2^t) and of a merge pass (layers
+// t-1 .. 0 of one stage p > t).
+std::vector<Round> tile_rounds(int t, int e);
+std::vector<Round> merge_rounds(int t, int e, int p);
+
+// Whole-array plan.  variant: 0/1 force divergent/melded everywhere, 2 uses
+// tn.var per pass kind.  map_in/map_out: key transforms of the first load and
+// last store.  Fills `out` (keys/vals pointers left null).
+bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, const Tuning& tn,
+                int variant, uint32_t map_in, uint32_t map_out, size_t smem_limit);
+
+std::string describe(const std::vector<Launch>& plan);
+
+}  // namespace darm
