@@ -26,6 +26,12 @@ const void* kernel_fn(KeyKind kk, bool has_vals, int loge, int variant) {
   return e.fn;
 }
 
+const void* fixed_kernel_fn(KeyKind kk, bool has_vals, int loge, int logt, int variant, bool merge) {
+  KernelEntry e = (kk == KEY_U32) ? tile_kernel_u32(has_vals, loge, logt, variant, merge)
+                                  : tile_kernel_u64(has_vals, loge, logt, variant, merge);
+  return e.fn;
+}
+
 int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_t* vals,
                 cudaStream_t stream) {
   const bool has_vals = vals != nullptr;
@@ -34,7 +40,9 @@ int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_
     P.keys = keys;
     P.vals = vals;
     P.status = g_ctx.d_status;
-    const void* fn = kernel_fn(kk, has_vals, L.loge, L.variant);
+    const void* fn = L.fixed ? fixed_kernel_fn(kk, has_vals, L.loge, int(L.P.b), L.variant,
+                                               L.kind == PASS_MERGE)
+                             : kernel_fn(kk, has_vals, L.loge, L.variant);
     if (!fn) return DARM_ERR_INVALID_ARG;
     void* args[] = {&P};
     cudaError_t err = cudaLaunchKernel(fn, dim3(L.grid), dim3(L.threads), args, L.smem, stream);
@@ -64,7 +72,7 @@ const std::vector<Launch>* cached_plan(KeyKind kk, bool has_vals, int m, int var
                                        uint32_t map_in, uint32_t map_out) {
   const Tuning tn = tuning_for(kk, has_vals, m);
   PlanKey key{int(kk), int(has_vals), m, variant, map_in, map_out, tn.t, tn.e1, tn.e2, tn.c2,
-              tn.var[0] * 4 + tn.var[1] * 2 + tn.var[2]};
+              tn.w2, tn.var[0] * 4 + tn.var[1] * 2 + tn.var[2]};
   std::lock_guard<std::mutex> lk(g_ctx.mu);
   auto it = g_ctx.plans.find(key);
   if (it != g_ctx.plans.end()) return &it->second;
@@ -125,6 +133,8 @@ int darm_sort_init(int device, size_t workspace_bytes) {
   g_ctx.smem_limit = size_t(optin);
   for_each_kernel_u32(set_smem_attr, &optin);
   for_each_kernel_u64(set_smem_attr, &optin);
+  for_each_tile_kernel_u32(set_smem_attr, &optin);
+  for_each_tile_kernel_u64(set_smem_attr, &optin);
   if (cudaMalloc(&g_ctx.d_status, sizeof(int)) != cudaSuccess) return DARM_ERR_OOM;
   if (cudaMemset(g_ctx.d_status, 0, sizeof(int)) != cudaSuccess) return DARM_ERR_CUDA;
   if (cudaStreamCreateWithFlags(&g_ctx.host_stream, cudaStreamNonBlocking) != cudaSuccess)

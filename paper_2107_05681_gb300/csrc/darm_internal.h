@@ -15,7 +15,7 @@
 namespace darm {
 
 // Everything that identifies a compiled whole-array plan.
-using PlanKey = std::tuple<int, int, int, int, uint32_t, uint32_t, int, int, int, int, int>;
+using PlanKey = std::tuple<int, int, int, int, uint32_t, uint32_t, int, int, int, int, int, int>;
 
 struct Context {
   bool inited = false;
@@ -36,6 +36,7 @@ struct Context {
 extern Context g_ctx;
 
 const void* kernel_fn(KeyKind kk, bool has_vals, int loge, int variant);
+const void* fixed_kernel_fn(KeyKind kk, bool has_vals, int loge, int logt, int variant, bool merge);
 int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_t* vals,
                 cudaStream_t stream);
 Tuning tuning_for(KeyKind kk, bool has_vals, int m);

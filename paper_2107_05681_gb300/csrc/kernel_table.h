@@ -16,9 +16,16 @@ struct KernelEntry {
 KernelEntry kernel_u32(bool has_vals, int loge, int var);
 KernelEntry kernel_u64(bool has_vals, int loge, int var);
 
+// Tile / merge kernels with a compile-time schedule for one tile size
+// (tile_kernel.cuh); {nullptr, 0} when that combination is not built.
+KernelEntry tile_kernel_u32(bool has_vals, int loge, int logt, int var, bool merge);
+KernelEntry tile_kernel_u64(bool has_vals, int loge, int logt, int var, bool merge);
+
 // Call fn(kernel address, ctx) for every instantiation (used to configure
 // shared-memory limits once per device).
 void for_each_kernel_u32(void (*fn)(const void*, void*), void* ctx);
 void for_each_kernel_u64(void (*fn)(const void*, void*), void* ctx);
+void for_each_tile_kernel_u32(void (*fn)(const void*, void*), void* ctx);
+void for_each_tile_kernel_u64(void (*fn)(const void*, void*), void* ctx);
 
 }  // namespace darm

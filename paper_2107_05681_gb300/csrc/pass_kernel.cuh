@@ -28,11 +28,16 @@
 //     bit (the small stages inside a tile, like Fig. 1's k < 32);
 //   - DIVERGENT wraps the whole round body (loads, compares, swaps,
 //     stores) in Fig. 1's if/else, one full copy per direction;
-//   - MELDED is that region after DARM's region-region meld (Section IV-G):
-//     the loads and stores of both sides are aligned into one copy, the two
-//     compares (< and >) stay unaligned, and a select on the direction picks
-//     the swap condition (Algorithm 2, SetOperands), so the warp reconverges
-//     before the swap.
+//   - MELDED is that region after DARM's region-region meld (Section IV-D,
+//     IV-G): the loads and stores of both sides are aligned into one copy;
+//     the two compares (key[l] < key[i] on one side, key[l] > key[i] on the
+//     other) are aligned as one compare whose differing operands are chosen
+//     by the direction (Algorithm 2, SetOperands) - the descending side's
+//     keys enter complemented, x -> ~x, which reverses unsigned order - so
+//     the warp reconverges before the swap.
+//   The planner marks the rounds in which bit k can differ between lanes of
+//   a warp; elsewhere the branch is warp-uniform, i.e. not a divergent
+//   region (Definition 5), and both forms keep the plain branch.
 // Stages whose direction bit is inside the thread's registers (k < E) have
 // a compile-time direction per register pair and no branch in either form.
 #pragma once
@@ -59,7 +64,8 @@ struct Round {
   uint8_t cnt;   // layers run: window bits a+LOGE-1 down to a+LOGE-cnt
   uint8_t src;   // Loc the round loads from
   uint8_t dst;   // Loc the round stores to
-  uint8_t pad0, pad1;
+  uint8_t lanediv;  // 1: the direction can differ between lanes of a warp
+  uint8_t pad;
 };
 
 // Key transforms applied on the first load / undone on the last store.
@@ -163,14 +169,22 @@ __device__ __forceinline__ void ce_side(K& a, K& b, uint32_t& va, uint32_t& vb) 
   cswap<K, V>(ASC ? (b < a) : (b > a), a, b, va, vb);
 }
 
-// The melded compare-exchange: both compares execute (the unaligned
-// instructions of the two sides) and a select on the direction picks the
-// swap condition.
-template <typename K, bool V>
-__device__ __forceinline__ void ce_melded(bool asc, K& a, K& b, uint32_t& va, uint32_t& vb) {
-  const bool lt = b < a;
-  const bool gt = b > a;
-  cswap<K, V>(asc ? lt : gt, a, b, va, vb);
+// ---------------------------------------------------------------------------
+// shared-memory layout
+// ---------------------------------------------------------------------------
+
+// Element l of a block lives at word phys(l) = l + 4 * (l / 32): four pad
+// words after every 32 elements.  With this layout
+//   - a warp whose lanes take 32 consecutive elements (window above bit 4)
+//     hits 32 different banks;
+//   - a warp whose lanes each take E consecutive elements (the bottom
+//     window) reads them as 16-byte vectors without bank conflicts;
+//   - the offset of register r in a window at bit a >= 5 is r * (2^a +
+//     2^(a-3)), a multiply-add instead of bit twiddling.
+__device__ __forceinline__ uint32_t phys(uint32_t l) { return l + ((l >> 5) << 2); }
+
+__host__ __device__ constexpr uint32_t smem_words(uint32_t elems) {
+  return elems + ((elems >> 5) << 2) + 4;
 }
 
 // ---------------------------------------------------------------------------
@@ -178,62 +192,88 @@ __device__ __forceinline__ void ce_melded(bool asc, K& a, K& b, uint32_t& va, ui
 // ---------------------------------------------------------------------------
 
 struct RoundAddr {
-  uint32_t g_t;  // index-in-array bits contributed by the thread and block
-  uint32_t s_t;  // swizzled shared-memory index of the thread part
-  uint32_t a;    // window position
-  uint32_t c, w0;
+  uint32_t g_t;     // index within the segment of the thread's register 0
+  uint32_t gsh;     // register r sits at g_t + (r << gsh) (non-vector rounds)
+  uint32_t s_base;  // phys() of the thread's register 0
+  uint32_t a;       // window position (local bit)
+  uint32_t stride;  // phys offset per register when a >= 5
 };
 
 __device__ __forceinline__ uint32_t gmap(uint32_t l, uint32_t c, uint32_t w0) {
   return (l & ((1u << c) - 1u)) | ((l >> c) << w0);
 }
 
-template <int LOGE>
-__device__ __forceinline__ uint32_t reg_g(const RoundAddr& A, int r) {
-  return gmap(uint32_t(r) << A.a, A.c, A.w0);
-}
-template <int LOGE>
-__device__ __forceinline__ uint32_t reg_s(const RoundAddr& A, int r) {
-  return swz(uint32_t(r) << A.a);
-}
+// XOR of a key with the direction mask (melded rounds) after the key map.
+template <typename K>
+__device__ __forceinline__ K kx(K x, K m) { return x ^ m; }
 
-// Load the thread's E elements for a round.  REV loads in the opposite
-// register order (used by the descending side of the divergent form so that
-// the compiler cannot hoist the two sides' identical leading loads out of
-// the branch, which would be a partial meld of exactly the code compared).
+// Load the thread's E elements of a round.  `m` is XORed into every key
+// (all-ones turns a descending compare-exchange into an ascending one).  REV
+// loads in the opposite register order: the descending side of the
+// divergent form uses it so that the compiler cannot hoist the two sides'
+// identical leading loads out of the branch (that would be a partial meld of
+// exactly the code being compared).
 template <typename K, bool V, int LOGE, bool REV>
 __device__ __forceinline__ void load_elems(K (&kr)[1 << LOGE], uint32_t (&vr)[1 << LOGE],
                                            uint8_t src, bool vec, const RoundAddr& A,
                                            const K* __restrict__ gk,
                                            const uint32_t* __restrict__ gv,
-                                           const K* sk, const uint32_t* sv, uint32_t mapf) {
+                                           const K* sk, const uint32_t* sv, uint32_t mapf, K m) {
   constexpr int E = 1 << LOGE;
+  constexpr int KPV = 16 / sizeof(K);  // keys per 16-byte vector
   if (src == LOC_GLOBAL) {
-    if (vec) {
-      // the window is the low LOGE bits of g: E consecutive elements
-      constexpr int KPV = 16 / sizeof(K);  // keys per 16-byte vector
-      if constexpr (E >= KPV) {
+    if (vec && E >= KPV) {
 #pragma unroll
-        for (int q0 = 0; q0 < E / KPV; ++q0) {
-          const int q = REV ? (E / KPV - 1 - q0) : q0;
-          const uint4 w = *reinterpret_cast<const uint4*>(gk + A.g_t + q * KPV);
-          const K* wk = reinterpret_cast<const K*>(&w);
+      for (int q0 = 0; q0 < E / KPV; ++q0) {
+        const int q = REV ? (E / KPV - 1 - q0) : q0;
+        const uint4 w = *reinterpret_cast<const uint4*>(gk + A.g_t + q * KPV);
+        const K* wk = reinterpret_cast<const K*>(&w);
 #pragma unroll
-          for (int u = 0; u < KPV; ++u) kr[q * KPV + u] = key_in<K>(wk[u], mapf);
+        for (int u = 0; u < KPV; ++u) kr[q * KPV + u] = kx(key_in<K>(wk[u], mapf), m);
+      }
+    } else {
+#pragma unroll
+      for (int r0 = 0; r0 < E; ++r0) {
+        const int r = REV ? (E - 1 - r0) : r0;
+        kr[r] = kx(key_in<K>(gk[A.g_t + (uint32_t(r) << A.gsh)], mapf), m);
+      }
+    }
+    if (V) {
+      if (vec && E >= 4) {
+#pragma unroll
+        for (int q0 = 0; q0 < E / 4; ++q0) {
+          const int q = REV ? (E / 4 - 1 - q0) : q0;
+          const uint4 w = *reinterpret_cast<const uint4*>(gv + A.g_t + q * 4);
+          vr[q * 4 + 0] = w.x;
+          vr[q * 4 + 1] = w.y;
+          vr[q * 4 + 2] = w.z;
+          vr[q * 4 + 3] = w.w;
         }
       } else {
 #pragma unroll
         for (int r0 = 0; r0 < E; ++r0) {
           const int r = REV ? (E - 1 - r0) : r0;
-          kr[r] = key_in<K>(gk[A.g_t + r], mapf);
+          vr[r] = gv[A.g_t + (uint32_t(r) << A.gsh)];
         }
+      }
+    }
+  } else {
+    if (A.a == 0 && E >= KPV) {
+      // bottom window: the thread's E elements are consecutive in phys space
+#pragma unroll
+      for (int q0 = 0; q0 < E / KPV; ++q0) {
+        const int q = REV ? (E / KPV - 1 - q0) : q0;
+        const uint4 w = *reinterpret_cast<const uint4*>(sk + A.s_base + q * KPV);
+        const K* wk = reinterpret_cast<const K*>(&w);
+#pragma unroll
+        for (int u = 0; u < KPV; ++u) kr[q * KPV + u] = kx(wk[u], m);
       }
       if (V) {
         if constexpr (E >= 4) {
 #pragma unroll
           for (int q0 = 0; q0 < E / 4; ++q0) {
             const int q = REV ? (E / 4 - 1 - q0) : q0;
-            const uint4 w = *reinterpret_cast<const uint4*>(gv + A.g_t + q * 4);
+            const uint4 w = *reinterpret_cast<const uint4*>(sv + A.s_base + q * 4);
             vr[q * 4 + 0] = w.x;
             vr[q * 4 + 1] = w.y;
             vr[q * 4 + 2] = w.z;
@@ -243,26 +283,27 @@ __device__ __forceinline__ void load_elems(K (&kr)[1 << LOGE], uint32_t (&vr)[1 
 #pragma unroll
           for (int r0 = 0; r0 < E; ++r0) {
             const int r = REV ? (E - 1 - r0) : r0;
-            vr[r] = gv[A.g_t + r];
+            vr[r] = sv[A.s_base + uint32_t(r)];
           }
         }
+      }
+    } else if (A.a >= 5) {
+      // lanes take consecutive elements; register r is r * stride words away
+#pragma unroll
+      for (int r0 = 0; r0 < E; ++r0) {
+        const int r = REV ? (E - 1 - r0) : r0;
+        const uint32_t si = A.s_base + uint32_t(r) * A.stride;
+        kr[r] = kx(sk[si], m);
+        if (V) vr[r] = sv[si];
       }
     } else {
 #pragma unroll
       for (int r0 = 0; r0 < E; ++r0) {
         const int r = REV ? (E - 1 - r0) : r0;
-        const uint32_t g = A.g_t + reg_g<LOGE>(A, r);
-        kr[r] = key_in<K>(gk[g], mapf);
-        if (V) vr[r] = gv[g];
+        const uint32_t si = A.s_base + phys(uint32_t(r) << A.a);
+        kr[r] = kx(sk[si], m);
+        if (V) vr[r] = sv[si];
       }
-    }
-  } else {
-#pragma unroll
-    for (int r0 = 0; r0 < E; ++r0) {
-      const int r = REV ? (E - 1 - r0) : r0;
-      const uint32_t si = A.s_t ^ reg_s<LOGE>(A, r);
-      kr[r] = sk[si];
-      if (V) vr[r] = sv[si];
     }
   }
 }
@@ -271,27 +312,57 @@ template <typename K, bool V, int LOGE, bool REV>
 __device__ __forceinline__ void store_elems(const K (&kr)[1 << LOGE], const uint32_t (&vr)[1 << LOGE],
                                             uint8_t dst, bool vec, const RoundAddr& A,
                                             K* __restrict__ gk, uint32_t* __restrict__ gv,
-                                            K* sk, uint32_t* sv, uint32_t mapf) {
+                                            K* sk, uint32_t* sv, uint32_t mapf, K m) {
   constexpr int E = 1 << LOGE;
+  constexpr int KPV = 16 / sizeof(K);
   if (dst == LOC_GLOBAL) {
-    if (vec) {
-      constexpr int KPV = 16 / sizeof(K);
-      if constexpr (E >= KPV) {
+    if (vec && E >= KPV) {
 #pragma unroll
-        for (int q0 = 0; q0 < E / KPV; ++q0) {
-          const int q = REV ? (E / KPV - 1 - q0) : q0;
+      for (int q0 = 0; q0 < E / KPV; ++q0) {
+        const int q = REV ? (E / KPV - 1 - q0) : q0;
+        uint4 w;
+        K* wk = reinterpret_cast<K*>(&w);
+#pragma unroll
+        for (int u = 0; u < KPV; ++u) wk[u] = key_out<K>(kx(kr[q * KPV + u], m), mapf);
+        *reinterpret_cast<uint4*>(gk + A.g_t + q * KPV) = w;
+      }
+    } else {
+#pragma unroll
+      for (int r0 = 0; r0 < E; ++r0) {
+        const int r = REV ? (E - 1 - r0) : r0;
+        gk[A.g_t + (uint32_t(r) << A.gsh)] = key_out<K>(kx(kr[r], m), mapf);
+      }
+    }
+    if (V) {
+      if (vec && E >= 4) {
+#pragma unroll
+        for (int q0 = 0; q0 < E / 4; ++q0) {
+          const int q = REV ? (E / 4 - 1 - q0) : q0;
           uint4 w;
-          K* wk = reinterpret_cast<K*>(&w);
-#pragma unroll
-          for (int u = 0; u < KPV; ++u) wk[u] = key_out<K>(kr[q * KPV + u], mapf);
-          *reinterpret_cast<uint4*>(gk + A.g_t + q * KPV) = w;
+          w.x = vr[q * 4 + 0];
+          w.y = vr[q * 4 + 1];
+          w.z = vr[q * 4 + 2];
+          w.w = vr[q * 4 + 3];
+          *reinterpret_cast<uint4*>(gv + A.g_t + q * 4) = w;
         }
       } else {
 #pragma unroll
         for (int r0 = 0; r0 < E; ++r0) {
           const int r = REV ? (E - 1 - r0) : r0;
-          gk[A.g_t + r] = key_out<K>(kr[r], mapf);
+          gv[A.g_t + (uint32_t(r) << A.gsh)] = vr[r];
         }
+      }
+    }
+  } else {
+    if (A.a == 0 && E >= KPV) {
+#pragma unroll
+      for (int q0 = 0; q0 < E / KPV; ++q0) {
+        const int q = REV ? (E / KPV - 1 - q0) : q0;
+        uint4 w;
+        K* wk = reinterpret_cast<K*>(&w);
+#pragma unroll
+        for (int u = 0; u < KPV; ++u) wk[u] = kx(kr[q * KPV + u], m);
+        *reinterpret_cast<uint4*>(sk + A.s_base + q * KPV) = w;
       }
       if (V) {
         if constexpr (E >= 4) {
@@ -303,32 +374,32 @@ __device__ __forceinline__ void store_elems(const K (&kr)[1 << LOGE], const uint
             w.y = vr[q * 4 + 1];
             w.z = vr[q * 4 + 2];
             w.w = vr[q * 4 + 3];
-            *reinterpret_cast<uint4*>(gv + A.g_t + q * 4) = w;
+            *reinterpret_cast<uint4*>(sv + A.s_base + q * 4) = w;
           }
         } else {
 #pragma unroll
           for (int r0 = 0; r0 < E; ++r0) {
             const int r = REV ? (E - 1 - r0) : r0;
-            gv[A.g_t + r] = vr[r];
+            sv[A.s_base + uint32_t(r)] = vr[r];
           }
         }
+      }
+    } else if (A.a >= 5) {
+#pragma unroll
+      for (int r0 = 0; r0 < E; ++r0) {
+        const int r = REV ? (E - 1 - r0) : r0;
+        const uint32_t si = A.s_base + uint32_t(r) * A.stride;
+        sk[si] = kx(kr[r], m);
+        if (V) sv[si] = vr[r];
       }
     } else {
 #pragma unroll
       for (int r0 = 0; r0 < E; ++r0) {
         const int r = REV ? (E - 1 - r0) : r0;
-        const uint32_t g = A.g_t + reg_g<LOGE>(A, r);
-        gk[g] = key_out<K>(kr[r], mapf);
-        if (V) gv[g] = vr[r];
+        const uint32_t si = A.s_base + phys(uint32_t(r) << A.a);
+        sk[si] = kx(kr[r], m);
+        if (V) sv[si] = vr[r];
       }
-    }
-  } else {
-#pragma unroll
-    for (int r0 = 0; r0 < E; ++r0) {
-      const int r = REV ? (E - 1 - r0) : r0;
-      const uint32_t si = A.s_t ^ reg_s<LOGE>(A, r);
-      sk[si] = kr[r];
-      if (V) sv[si] = vr[r];
     }
   }
 }
@@ -355,23 +426,6 @@ __device__ __forceinline__ void window_side(K (&kr)[1 << LOGE], uint32_t (&vr)[1
   }
 }
 
-template <typename K, bool V, int LOGE>
-__device__ __forceinline__ void window_melded(bool asc, K (&kr)[1 << LOGE], uint32_t (&vr)[1 << LOGE],
-                                              int cnt) {
-  constexpr int E = 1 << LOGE;
-#pragma unroll
-  for (int i = 0; i < LOGE; ++i) {
-    if (i < cnt) {
-      const int q = LOGE - 1 - i;
-#pragma unroll
-      for (int r = 0; r < E; ++r) {
-        if ((r >> q) & 1) continue;
-        ce_melded<K, V>(asc, kr[r], kr[r | (1 << q)], vr[r], vr[r | (1 << q)]);
-      }
-    }
-  }
-}
-
 // Stages k = 2 .. E/2 on E consecutive elements: the direction bit lies in
 // the register index, so each pair's direction is a compile-time constant
 // (stage k == cap, the final stage of a tiny segment, is ascending).
@@ -388,10 +442,7 @@ __device__ __forceinline__ void phase_a_small(K (&kr)[1 << LOGE], uint32_t (&vr)
 #pragma unroll
         for (int r = 0; r < E; ++r) {
           if ((r >> q) & 1) continue;
-          const bool asc_pair = ((r >> p) & 1) == 0;
-          if (asc_pair)
-            ce_side<K, V, true>(kr[r], kr[r | (1 << q)], vr[r], vr[r | (1 << q)]);
-          else if (final_stage)
+          if (((r >> p) & 1) == 0 || final_stage)
             ce_side<K, V, true>(kr[r], kr[r | (1 << q)], vr[r], vr[r | (1 << q)]);
           else
             ce_side<K, V, false>(kr[r], kr[r | (1 << q)], vr[r], vr[r | (1 << q)]);
@@ -411,11 +462,11 @@ template <typename K>
 __device__ __forceinline__ K key_max() { return ~K(0); }
 
 template <typename K, bool V, int LOGE, int VAR, int MAXT>
-__global__ void __launch_bounds__(MAXT) darm_pass_kernel(const __grid_constant__ PassParams P) {
+__global__ void __launch_bounds__(MAXT, 1) darm_pass_kernel(const __grid_constant__ PassParams P) {
   constexpr int E = 1 << LOGE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   K* sk = reinterpret_cast<K*>(smem_raw);
-  uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + (size_t(sizeof(K)) << P.b));
+  uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + size_t(sizeof(K)) * smem_words(1u << P.b));
 
   K* __restrict__ gk = reinterpret_cast<K*>(P.keys);
   uint32_t* __restrict__ gv = P.vals;
@@ -451,14 +502,15 @@ __global__ void __launch_bounds__(MAXT) darm_pass_kernel(const __grid_constant__
     const bool last = (rd + 1 == nrounds);
     const uint8_t src = R.src;
     const uint8_t dst = last ? uint8_t(LOC_GLOBAL) : R.dst;
-    RoundAddr A;
-    A.a = R.a;
-    A.c = P.c;
-    A.w0 = P.w0;
-    const uint32_t tl = (tid & ((1u << R.a) - 1u)) | ((tid >> R.a) << (R.a + LOGE));
+    const uint32_t a = R.a;
+    const uint32_t tl = (tid & ((1u << a) - 1u)) | ((tid >> a) << (a + LOGE));
     const uint32_t g_full = gmap(tl, P.c, P.w0) | gblk;  // index within the segment(s)
-    A.s_t = swz(tl);
-    const bool vec = (R.a == 0) && (P.c >= uint32_t(LOGE));
+    RoundAddr A;
+    A.a = a;
+    A.gsh = (a >= P.c) ? (a - P.c + P.w0) : a;
+    A.s_base = phys(tl);
+    A.stride = (a >= 5) ? ((1u << a) + (1u << (a - 3))) : 0u;
+    const bool vec = (a == 0) && (P.c >= uint32_t(LOGE));
     uint32_t min_ = 0, mout = 0;
     K* bk = gk;
     uint32_t* bv = gv;
@@ -480,9 +532,12 @@ __global__ void __launch_bounds__(MAXT) darm_pass_kernel(const __grid_constant__
     }
     // direction bits are read from the index within the segment
     const uint32_t g_dir = g_full & capmask;
+    // the planner marks rounds whose direction can differ between the
+    // lanes of a warp; only those are melded
+    const bool lane_divergent = R.lanediv != 0;
 
     if (R.kind == RK_PHASE_A) {
-      load_elems<K, V, LOGE, false>(kr, vr, src, vec, A, bk, bv, sk, sv, min_);
+      load_elems<K, V, LOGE, false>(kr, vr, src, vec, A, bk, bv, sk, sv, min_, K(0));
       if (fill) {
         // segment padding: positions at or beyond the real length take the
         // largest key; a real key equal to it is a collision when a payload
@@ -504,43 +559,57 @@ __global__ void __launch_bounds__(MAXT) darm_pass_kernel(const __grid_constant__
       if (uint32_t(LOGE) <= log2cap) {
         // stage k = E: the direction bit is the lowest thread bit
         const bool asc = ((g_dir & uint32_t(E) & capmask) == 0u);
-        if (VAR == kDivergent) {
+        if (VAR == kDivergent || !lane_divergent) {
           if (asc)
             window_side<K, V, LOGE, true>(kr, vr, LOGE);
           else
             window_side<K, V, LOGE, false>(kr, vr, LOGE);
         } else {
-          window_melded<K, V, LOGE>(asc, kr, vr, LOGE);
+          const K m = asc ? K(0) : ~K(0);
+#pragma unroll
+          for (int r = 0; r < E; ++r) kr[r] ^= m;
+          window_side<K, V, LOGE, true>(kr, vr, LOGE);
+#pragma unroll
+          for (int r = 0; r < E; ++r) kr[r] ^= m;
         }
       }
-      store_elems<K, V, LOGE, false>(kr, vr, dst, vec, A, bk, bv, sk, sv, mout);
+      store_elems<K, V, LOGE, false>(kr, vr, dst, vec, A, bk, bv, sk, sv, mout, K(0));
     } else {
       const bool asc = ((g_dir & (1u << R.p) & capmask) == 0u);
       const int cnt = R.cnt;
-      if (VAR == kDivergent) {
+      if (VAR == kDivergent || !lane_divergent) {
+        // Fig. 1: one full copy of the body per direction
         if (asc) {
-          load_elems<K, V, LOGE, false>(kr, vr, src, vec, A, bk, bv, sk, sv, min_);
+          load_elems<K, V, LOGE, false>(kr, vr, src, vec, A, bk, bv, sk, sv, min_, K(0));
           window_side<K, V, LOGE, true>(kr, vr, cnt);
-          store_elems<K, V, LOGE, false>(kr, vr, dst, vec, A, bk, bv, sk, sv, mout);
+          store_elems<K, V, LOGE, false>(kr, vr, dst, vec, A, bk, bv, sk, sv, mout, K(0));
         } else {
-          load_elems<K, V, LOGE, true>(kr, vr, src, vec, A, bk, bv, sk, sv, min_);
+          load_elems<K, V, LOGE, true>(kr, vr, src, vec, A, bk, bv, sk, sv, min_, K(0));
           window_side<K, V, LOGE, false>(kr, vr, cnt);
-          store_elems<K, V, LOGE, true>(kr, vr, dst, vec, A, bk, bv, sk, sv, mout);
+          store_elems<K, V, LOGE, true>(kr, vr, dst, vec, A, bk, bv, sk, sv, mout, K(0));
         }
       } else {
-        load_elems<K, V, LOGE, false>(kr, vr, src, vec, A, bk, bv, sk, sv, min_);
-        window_melded<K, V, LOGE>(asc, kr, vr, cnt);
-        store_elems<K, V, LOGE, false>(kr, vr, dst, vec, A, bk, bv, sk, sv, mout);
+        // melded: one copy of the loads, compares and stores.  The two sides'
+        // compares (key[l] < key[i] and key[l] > key[i]) are aligned by
+        // selecting their operands: the descending side's keys enter
+        // complemented (x -> ~x reverses unsigned order), so both sides run
+        // the same ascending compare-exchange, and the stores undo it.
+        const K m = asc ? K(0) : ~K(0);
+        load_elems<K, V, LOGE, false>(kr, vr, src, vec, A, bk, bv, sk, sv, min_, m);
+        window_side<K, V, LOGE, true>(kr, vr, cnt);
+        store_elems<K, V, LOGE, false>(kr, vr, dst, vec, A, bk, bv, sk, sv, mout, m);
       }
     }
     if (dst == LOC_SMEM) __syncthreads();
   }
 }
 
-// Largest block size a (K, V, E) instantiation is compiled for.
+// Largest block size a (K, V, E) instantiation is compiled for: 1024
+// threads (64 registers each) while a thread's elements fit in 32 words,
+// else 512 threads with up to 128 registers.
 template <typename K, bool V, int LOGE>
 constexpr int max_threads_for() {
-  return ((1 << LOGE) * (int(sizeof(K) / 4) + (V ? 1 : 0)) <= 16) ? 1024 : 512;
+  return ((1 << LOGE) * (int(sizeof(K) / 4) + (V ? 1 : 0)) <= 32) ? 1024 : 512;
 }
 
 }  // namespace darm

@@ -5,8 +5,32 @@
 
 #include "kernel_table.h"
 #include "plan.h"
+#include "tile_kernel.cuh"
 
 namespace darm {
+
+int fixed_schedule_rounds(int logt, int loge, bool merge, SRound* out, int cap);
+
+// A compile-time-schedule kernel is used only if one was built for this
+// (key, payload, E, T) and its schedule equals the planner's round list.
+static bool has_fixed(KeyKind kk, bool has_vals, int loge, int logt) {
+  KernelEntry e = (kk == KEY_U32) ? tile_kernel_u32(has_vals, loge, logt, 1, false)
+                                  : tile_kernel_u64(has_vals, loge, logt, 1, false);
+  if (e.fn == nullptr) return false;
+  for (int merge = 0; merge < 2; ++merge) {
+    SRound sr[kMaxRounds];
+    const int n = fixed_schedule_rounds(logt, loge, merge != 0, sr, kMaxRounds);
+    const std::vector<Round> rs = merge ? merge_rounds(logt, loge, logt + 1) : tile_rounds(logt, loge);
+    if (n != int(rs.size())) return false;
+    for (int i = 0; i < n; ++i) {
+      const Round& r = rs[i];
+      if (sr[i].kind != r.kind || sr[i].a != r.a || sr[i].cnt != r.cnt || sr[i].src != r.src ||
+          sr[i].dst != r.dst || (!merge && sr[i].p != r.p))
+        return false;
+    }
+  }
+  return true;
+}
 
 static int max_threads(KeyKind kk, bool has_vals, int loge) {
   KernelEntry e = (kk == KEY_U32) ? kernel_u32(has_vals, loge, 1) : kernel_u64(has_vals, loge, 1);
@@ -19,18 +43,21 @@ Tuning default_tuning(KeyKind kk, bool has_vals) {
   if (words == 1) {
     tn.t = 14;  // 16 Ki uint32 keys = 64 KiB of shared memory per tile
     tn.e1 = 4;
-    tn.e2 = 5;
+    tn.e2 = 4;
     tn.c2 = 8;
+    tn.w2 = 2;
   } else if (words == 2) {
     tn.t = 13;  // 8 Ki elements of 8 bytes = 64 KiB
     tn.e1 = 4;
     tn.e2 = 4;
     tn.c2 = 8;
+    tn.w2 = 2;
   } else {
     tn.t = 12;  // 4 Ki elements of 12 bytes = 48 KiB
     tn.e1 = 3;
     tn.e2 = 3;
     tn.c2 = 8;
+    tn.w2 = 2;
   }
   tn.var[0] = tn.var[1] = tn.var[2] = kMelded;
   return tn;
@@ -48,7 +75,7 @@ bool fit_tuning(Tuning& tn, KeyKind kk, bool has_vals, int m, size_t smem_limit)
   tn.e2 = std::max(1, std::min(tn.e2, 5));
   tn.t = std::min(tn.t, m);
   // shared memory: one tile of keys + payload
-  while (tn.t > 1 && (size_t(elem_bytes(kk, has_vals)) << tn.t) > smem_limit) --tn.t;
+  while (tn.t > 1 && size_t(elem_bytes(kk, has_vals)) * smem_words(1u << tn.t) > smem_limit) --tn.t;
   tn.e1 = std::min(tn.e1, tn.t);
   if (tn.t >= 2) tn.e1 = std::max(tn.e1, 2);
   // block size of tile passes must fit the instantiation
@@ -64,6 +91,7 @@ bool fit_tuning(Tuning& tn, KeyKind kk, bool has_vals, int m, size_t smem_limit)
   // window passes: threads cover low bits, window of e2 bits
   tn.c2 = std::max(0, std::min(tn.c2, 10));
   while ((1 << tn.c2) > max_threads(kk, has_vals, tn.e2)) --tn.c2;
+  tn.w2 = std::max(1, std::min(tn.w2, 2));
   return true;
 }
 
@@ -116,6 +144,23 @@ std::vector<Round> merge_rounds(int t, int e, int p) {
   return rs;
 }
 
+// Lane bit j (thread-index bit j < 5) of a round with window a..a+e-1 maps
+// to local bit j (below the window) or j + e (above it).  The direction of
+// stage 2^p can differ within a warp when local bit p is one of them.
+static bool lane_divergent(int p, int a, int e, int b, int threads_log2) {
+  if (p >= b) return false;  // block-index bit: uniform per block
+  const int lanes = std::min(5, threads_log2);
+  for (int j = 0; j < lanes; ++j) {
+    const int pos = (j < a) ? j : j + e;
+    if (pos == p) return true;
+  }
+  return false;
+}
+
+static void mark_lanes(std::vector<Round>& rs, int e, int b, int threads_log2) {
+  for (Round& r : rs) r.lanediv = lane_divergent(r.p, r.a, e, b, threads_log2) ? 1 : 0;
+}
+
 static void set_rounds(PassParams& P, const std::vector<Round>& rs) {
   P.nrounds = uint32_t(rs.size());
   for (size_t i = 0; i < rs.size(); ++i) P.rounds[i] = rs[i];
@@ -137,17 +182,19 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
   Tuning tn = tn0;
   if (!fit_tuning(tn, kk, has_vals, m, smem_limit)) return false;
   const int t = tn.t, e1 = tn.e1, e2 = tn.e2;
-  const size_t tile_smem = size_t(elem_bytes(kk, has_vals)) << t;
+  const size_t tile_smem = size_t(elem_bytes(kk, has_vals)) * smem_words(1u << t);
 
   // tile pass
   {
     Launch L{};
     L.kind = PASS_TILE;
+    L.fixed = has_fixed(kk, has_vals, e1, t);
     L.loge = e1;
     L.variant = pick_var(variant, tn, PASS_TILE);
     L.grid = uint32_t(1u << (m - t));
     L.threads = 1u << (t - e1);
     std::vector<Round> rs = tile_rounds(t, e1);
+    mark_lanes(rs, e1, t, t - e1);
     L.smem = uses_smem(rs) ? tile_smem : 0;
     L.P.b = uint32_t(t);
     L.P.c = uint32_t(t);
@@ -160,44 +207,87 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
     out.push_back(L);
   }
   for (int p = t + 1; p <= m; ++p) {
-    // window passes over layer bits t .. p-1, highest window first
-    const int nbits = p - t;
-    const int nw = (nbits + e2 - 1) / e2;
-    for (int i = nw - 1; i >= 0; --i) {
-      const int lo = t + i * e2;
-      const int hi = std::min(t + (i + 1) * e2, p) - 1;
-      const int w0 = hi - e2 + 1;
-      const int c = std::min(tn.c2, w0);
+    // window passes over layer bits t .. p-1, highest bits first.  A pass
+    // covers up to w2 * e2 bits: one register window straight from HBM and
+    // back, or (w2 = 2) two windows with one exchange through shared memory,
+    // whose block holds 32 consecutive elements per window position so that
+    // every warp access stays coalesced.
+    const int c_sm = 5;
+    const bool two = tn.w2 >= 2 && (c_sm + 2 * e2 <= t);
+    const int w_max = two ? 2 * e2 : e2;
+    int hi = p - 1;
+    while (hi >= t) {
+      const int nbits = std::min(hi - t + 1, w_max);
+      const int lo = hi - nbits + 1;
+      const int nr = (nbits + e2 - 1) / e2;
       Launch L{};
       L.kind = PASS_WINDOW;
+      L.fixed = false;
       L.loge = e2;
       L.variant = pick_var(variant, tn, PASS_WINDOW);
-      L.threads = 1u << c;
-      L.grid = uint32_t(1u << (m - c - e2));
-      L.smem = 0;
-      L.P.b = uint32_t(c + e2);
-      L.P.c = uint32_t(c);
-      L.P.w0 = uint32_t(w0);
-      L.P.s = uint32_t(e2);
       L.P.log2cap = uint32_t(m);
-      Round r{};
-      r.kind = RK_WINDOW;
-      r.p = uint8_t(p);
-      r.a = uint8_t(c);
-      r.cnt = uint8_t(hi - lo + 1);
-      r.src = LOC_GLOBAL;
-      r.dst = LOC_GLOBAL;
-      set_rounds(L.P, std::vector<Round>{r});
+      if (nr == 1) {
+        const int w0 = hi - e2 + 1;
+        const int c = std::min(tn.c2, w0);
+        L.threads = 1u << c;
+        L.grid = uint32_t(1u << (m - c - e2));
+        L.smem = 0;
+        L.P.b = uint32_t(c + e2);
+        L.P.c = uint32_t(c);
+        L.P.w0 = uint32_t(w0);
+        L.P.s = uint32_t(e2);
+        Round r{};
+        r.kind = RK_WINDOW;
+        r.p = uint8_t(p);
+        r.a = uint8_t(c);
+        r.cnt = uint8_t(nbits);
+        r.src = LOC_GLOBAL;
+        r.dst = LOC_GLOBAL;
+        r.lanediv = 0;  // bit p lies above the window: one direction per block
+        set_rounds(L.P, std::vector<Round>{r});
+      } else {
+        const int sbits = nr * e2;
+        const int w0 = hi - sbits + 1;
+        const int c = c_sm;
+        const int b = c + sbits;
+        L.threads = 1u << (b - e2);
+        L.grid = uint32_t(1u << (m - b));
+        L.smem = size_t(elem_bytes(kk, has_vals)) * smem_words(1u << b);
+        L.P.b = uint32_t(b);
+        L.P.c = uint32_t(c);
+        L.P.w0 = uint32_t(w0);
+        L.P.s = uint32_t(sbits);
+        std::vector<Round> rs;
+        int top = b - 1;                 // local bit of layer hi
+        const int bottom = b - nbits;    // local bit of layer lo
+        for (int i = 0; i < nr; ++i) {
+          const int rhi = top - i * e2;
+          const int rlo = std::max(rhi - e2 + 1, bottom);
+          Round r{};
+          r.kind = RK_WINDOW;
+          r.p = uint8_t(p);
+          r.a = uint8_t(rhi - e2 + 1);
+          r.cnt = uint8_t(rhi - rlo + 1);
+          r.src = (i == 0) ? LOC_GLOBAL : LOC_SMEM;
+          r.dst = (i == nr - 1) ? LOC_GLOBAL : LOC_SMEM;
+          r.lanediv = 0;
+          rs.push_back(r);
+        }
+        set_rounds(L.P, rs);
+      }
       out.push_back(L);
+      hi = lo - 1;
     }
     // merge pass: layers t-1 .. 0 inside each tile
     Launch L{};
     L.kind = PASS_MERGE;
+    L.fixed = has_fixed(kk, has_vals, e1, t);
     L.loge = e1;
     L.variant = pick_var(variant, tn, PASS_MERGE);
     L.grid = uint32_t(1u << (m - t));
     L.threads = 1u << (t - e1);
     std::vector<Round> rs = merge_rounds(t, e1, p);
+    mark_lanes(rs, e1, t, t - e1);
     L.smem = uses_smem(rs) ? tile_smem : 0;
     L.P.b = uint32_t(t);
     L.P.c = uint32_t(t);
@@ -216,7 +306,7 @@ std::string describe(const std::vector<Launch>& plan) {
   std::ostringstream os;
   static const char* names[] = {"tile", "window", "merge"};
   for (const Launch& L : plan) {
-    os << names[L.kind] << " E=" << (1 << L.loge) << " var=" << L.variant << " grid=" << L.grid
+    os << names[L.kind] << (L.fixed ? "*" : "") << " E=" << (1 << L.loge) << " var=" << L.variant << " grid=" << L.grid
        << " threads=" << L.threads << " smem=" << L.smem << " b=" << L.P.b << " c=" << L.P.c
        << " w0=" << L.P.w0 << " rounds=" << L.P.nrounds << "\n";
   }

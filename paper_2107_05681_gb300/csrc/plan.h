@@ -30,12 +30,15 @@ struct Tuning {
   int t;      // log2 tile elements (tile and merge passes)
   int e1;     // log2 elements per thread in tile and merge passes
   int e2;     // log2 elements per thread in window passes
-  int c2;     // log2 threads per block in window passes
+  int c2;     // log2 threads per block in one-round window passes
+  int w2;     // register windows per window pass (1: registers only; 2: one
+              // shared-memory exchange, 2*e2 layers per HBM sweep)
   int var[3]; // variant per pass kind (used when DARM_AUTO is requested)
 };
 
 struct Launch {
   PassKind kind;
+  bool fixed;  // compile-time-schedule tile/merge kernel (tile_kernel.cuh)
   int loge;
   int variant;
   uint32_t grid;

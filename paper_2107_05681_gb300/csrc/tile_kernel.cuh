@@ -1,0 +1,401 @@
+// tile_kernel.cuh - tile and merge passes with their round schedule fixed
+// at compile time.
+//
+// Same network, rounds and direction handling as darm_pass_kernel
+// (pass_kernel.cuh), specialised for one tile size T = 2^LOGT and
+// E = 2^LOGE elements per thread: every window position, layer count and
+// direction bit is a template constant, so shared-memory and global offsets
+// of every register are immediates and the round loop disappears.
+//   MERGE = false  tile pass: stages k = 2 .. T (Phase A in registers for
+//                  k <= E, then register windows through shared memory);
+//   MERGE = true   merge pass of one stage k > T (runtime p): layers
+//                  j = T/2 .. 1 inside the tile, direction uniform per block.
+#pragma once
+
+#include "pass_kernel.cuh"
+
+namespace darm {
+
+struct SRound {
+  int kind;     // RK_PHASE_A or RK_WINDOW
+  int p;        // stage bit (tile pass; merge passes take p at run time)
+  int a;        // window position
+  int cnt;      // layers (top `cnt` window bits)
+  int src, dst; // Loc
+  int lanediv;  // direction can differ between lanes of a warp
+};
+
+template <int N>
+struct SSchedule {
+  SRound r[N];
+};
+
+__host__ __device__ constexpr int s_min(int x, int y) { return x < y ? x : y; }
+
+// Lane j of a round with window a..a+e-1 sits at local bit (j < a ? j : j + e).
+__host__ __device__ constexpr int s_lanediv(int p, int a, int e, int t) {
+  if (p >= t) return 0;
+  const int lanes = s_min(5, t - e);
+  for (int j = 0; j < lanes; ++j)
+    if (((j < a) ? j : j + e) == p) return 1;
+  return 0;
+}
+
+__host__ __device__ constexpr int tile_round_count(int t, int e) {
+  int n = 1;
+  for (int p = e + 1; p <= t; ++p) n += (p + e - 1) / e;
+  return n;
+}
+
+template <int T, int E>
+__host__ __device__ constexpr SSchedule<tile_round_count(T, E)> make_tile_schedule() {
+  SSchedule<tile_round_count(T, E)> s{};
+  int n = 0;
+  s.r[n++] = SRound{RK_PHASE_A, E, 0, E, LOC_GLOBAL, (T == E) ? LOC_GLOBAL : LOC_SMEM,
+                    (T > E) ? 1 : 0};
+  for (int p = E + 1; p <= T; ++p) {
+    const int nw = (p + E - 1) / E;
+    for (int i = nw - 1; i >= 0; --i) {
+      const int lo = i * E;
+      const int hi = s_min((i + 1) * E, p) - 1;
+      const int a = hi - E + 1;
+      s.r[n++] = SRound{RK_WINDOW, p, a, hi - lo + 1, LOC_SMEM, LOC_SMEM, s_lanediv(p, a, E, T)};
+    }
+  }
+  s.r[n - 1].dst = LOC_GLOBAL;
+  return s;
+}
+
+__host__ __device__ constexpr int merge_round_count(int t, int e) { return (t + e - 1) / e; }
+
+template <int T, int E>
+__host__ __device__ constexpr SSchedule<merge_round_count(T, E)> make_merge_schedule() {
+  SSchedule<merge_round_count(T, E)> s{};
+  int n = 0;
+  const int nw = (T + E - 1) / E;
+  for (int i = nw - 1; i >= 0; --i) {
+    const int lo = i * E;
+    const int hi = s_min((i + 1) * E, T) - 1;
+    s.r[n++] = SRound{RK_WINDOW, 0, hi - E + 1, hi - lo + 1, LOC_SMEM, LOC_SMEM, 0};
+  }
+  s.r[0].src = LOC_GLOBAL;
+  s.r[n - 1].dst = LOC_GLOBAL;
+  return s;
+}
+
+template <int T, int E, bool MERGE>
+struct Schedule;
+template <int T, int E>
+struct Schedule<T, E, false> {
+  static constexpr SSchedule<tile_round_count(T, E)> value = make_tile_schedule<T, E>();
+  static constexpr int count = tile_round_count(T, E);
+};
+template <int T, int E>
+struct Schedule<T, E, true> {
+  static constexpr SSchedule<merge_round_count(T, E)> value = make_merge_schedule<T, E>();
+  static constexpr int count = merge_round_count(T, E);
+};
+
+template <int I>
+struct IC {
+  static constexpr int value = I;
+};
+
+template <int I, int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(IC<I>{});
+    static_for<I + 1, N>(f);
+  }
+}
+
+// Static-offset element access: register r of a round with window A sits at
+// local index tl | (r << A); phys() is additive over disjoint bits, so its
+// shared-memory word is phys(tl) + phys(r << A), a compile-time offset.
+template <typename K, bool V, int LOGE, int A, bool REV>
+__device__ __forceinline__ void s_load(K (&kr)[1 << LOGE], uint32_t (&vr)[1 << LOGE], bool from_global,
+                                       const K* __restrict__ gk, const uint32_t* __restrict__ gv,
+                                       uint32_t g_t, const K* sk, const uint32_t* sv,
+                                       uint32_t s_base, uint32_t mapf, K m) {
+  constexpr int E = 1 << LOGE;
+  constexpr int KPV = 16 / sizeof(K);
+  if (from_global) {
+    if constexpr (A == 0 && E >= KPV) {
+#pragma unroll
+      for (int q0 = 0; q0 < E / KPV; ++q0) {
+        const int q = REV ? (E / KPV - 1 - q0) : q0;
+        const uint4 w = *reinterpret_cast<const uint4*>(gk + g_t + q * KPV);
+        const K* wk = reinterpret_cast<const K*>(&w);
+#pragma unroll
+        for (int u = 0; u < KPV; ++u) kr[q * KPV + u] = key_in<K>(wk[u], mapf) ^ m;
+      }
+      if constexpr (V && E >= 4) {
+#pragma unroll
+        for (int q0 = 0; q0 < E / 4; ++q0) {
+          const int q = REV ? (E / 4 - 1 - q0) : q0;
+          const uint4 w = *reinterpret_cast<const uint4*>(gv + g_t + q * 4);
+          vr[q * 4 + 0] = w.x;
+          vr[q * 4 + 1] = w.y;
+          vr[q * 4 + 2] = w.z;
+          vr[q * 4 + 3] = w.w;
+        }
+      } else if constexpr (V) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) vr[r] = gv[g_t + r];
+      }
+    } else {
+#pragma unroll
+      for (int r0 = 0; r0 < E; ++r0) {
+        const int r = REV ? (E - 1 - r0) : r0;
+        kr[r] = key_in<K>(gk[g_t + (uint32_t(r) << A)], mapf) ^ m;
+        if (V) vr[r] = gv[g_t + (uint32_t(r) << A)];
+      }
+    }
+  } else {
+    if constexpr (A == 0 && E >= KPV) {
+#pragma unroll
+      for (int q0 = 0; q0 < E / KPV; ++q0) {
+        const int q = REV ? (E / KPV - 1 - q0) : q0;
+        const uint4 w = *reinterpret_cast<const uint4*>(sk + s_base + q * KPV);
+        const K* wk = reinterpret_cast<const K*>(&w);
+#pragma unroll
+        for (int u = 0; u < KPV; ++u) kr[q * KPV + u] = wk[u] ^ m;
+      }
+      if constexpr (V && E >= 4) {
+#pragma unroll
+        for (int q0 = 0; q0 < E / 4; ++q0) {
+          const int q = REV ? (E / 4 - 1 - q0) : q0;
+          const uint4 w = *reinterpret_cast<const uint4*>(sv + s_base + q * 4);
+          vr[q * 4 + 0] = w.x;
+          vr[q * 4 + 1] = w.y;
+          vr[q * 4 + 2] = w.z;
+          vr[q * 4 + 3] = w.w;
+        }
+      } else if constexpr (V) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) vr[r] = sv[s_base + r];
+      }
+    } else {
+#pragma unroll
+      for (int r0 = 0; r0 < E; ++r0) {
+        const int r = REV ? (E - 1 - r0) : r0;
+        const uint32_t off = uint32_t(r << A) + ((uint32_t(r << A) >> 5) << 2);
+        kr[r] = sk[s_base + off] ^ m;
+        if (V) vr[r] = sv[s_base + off];
+      }
+    }
+  }
+}
+
+template <typename K, bool V, int LOGE, int A, bool REV>
+__device__ __forceinline__ void s_store(const K (&kr)[1 << LOGE], const uint32_t (&vr)[1 << LOGE],
+                                        bool to_global, K* __restrict__ gk, uint32_t* __restrict__ gv,
+                                        uint32_t g_t, K* sk, uint32_t* sv, uint32_t s_base,
+                                        uint32_t mapf, K m) {
+  constexpr int E = 1 << LOGE;
+  constexpr int KPV = 16 / sizeof(K);
+  if (to_global) {
+    if constexpr (A == 0 && E >= KPV) {
+#pragma unroll
+      for (int q0 = 0; q0 < E / KPV; ++q0) {
+        const int q = REV ? (E / KPV - 1 - q0) : q0;
+        uint4 w;
+        K* wk = reinterpret_cast<K*>(&w);
+#pragma unroll
+        for (int u = 0; u < KPV; ++u) wk[u] = key_out<K>(kr[q * KPV + u] ^ m, mapf);
+        *reinterpret_cast<uint4*>(gk + g_t + q * KPV) = w;
+      }
+      if constexpr (V && E >= 4) {
+#pragma unroll
+        for (int q0 = 0; q0 < E / 4; ++q0) {
+          const int q = REV ? (E / 4 - 1 - q0) : q0;
+          uint4 w;
+          w.x = vr[q * 4 + 0];
+          w.y = vr[q * 4 + 1];
+          w.z = vr[q * 4 + 2];
+          w.w = vr[q * 4 + 3];
+          *reinterpret_cast<uint4*>(gv + g_t + q * 4) = w;
+        }
+      } else if constexpr (V) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) gv[g_t + r] = vr[r];
+      }
+    } else {
+#pragma unroll
+      for (int r0 = 0; r0 < E; ++r0) {
+        const int r = REV ? (E - 1 - r0) : r0;
+        gk[g_t + (uint32_t(r) << A)] = key_out<K>(kr[r] ^ m, mapf);
+        if (V) gv[g_t + (uint32_t(r) << A)] = vr[r];
+      }
+    }
+  } else {
+    if constexpr (A == 0 && E >= KPV) {
+#pragma unroll
+      for (int q0 = 0; q0 < E / KPV; ++q0) {
+        const int q = REV ? (E / KPV - 1 - q0) : q0;
+        uint4 w;
+        K* wk = reinterpret_cast<K*>(&w);
+#pragma unroll
+        for (int u = 0; u < KPV; ++u) wk[u] = kr[q * KPV + u] ^ m;
+        *reinterpret_cast<uint4*>(sk + s_base + q * KPV) = w;
+      }
+      if constexpr (V && E >= 4) {
+#pragma unroll
+        for (int q0 = 0; q0 < E / 4; ++q0) {
+          const int q = REV ? (E / 4 - 1 - q0) : q0;
+          uint4 w;
+          w.x = vr[q * 4 + 0];
+          w.y = vr[q * 4 + 1];
+          w.z = vr[q * 4 + 2];
+          w.w = vr[q * 4 + 3];
+          *reinterpret_cast<uint4*>(sv + s_base + q * 4) = w;
+        }
+      } else if constexpr (V) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) sv[s_base + r] = vr[r];
+      }
+    } else {
+#pragma unroll
+      for (int r0 = 0; r0 < E; ++r0) {
+        const int r = REV ? (E - 1 - r0) : r0;
+        const uint32_t off = uint32_t(r << A) + ((uint32_t(r << A) >> 5) << 2);
+        sk[s_base + off] = kr[r] ^ m;
+        if (V) sv[s_base + off] = vr[r];
+      }
+    }
+  }
+}
+
+template <typename K, bool V, int LOGE, int LOGT, int VAR, bool MERGE, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) darm_tile_kernel(const __grid_constant__ PassParams P) {
+  constexpr int E = 1 << LOGE;
+  constexpr uint32_t SW = smem_words(1u << LOGT);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  K* sk = reinterpret_cast<K*>(smem_raw);
+  uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + sizeof(K) * SW);
+
+  K* __restrict__ gk = reinterpret_cast<K*>(P.keys);
+  uint32_t* __restrict__ gv = P.vals;
+  const uint32_t tid = threadIdx.x;
+
+  uint32_t blk = blockIdx.x;
+  uint32_t log2cap = P.log2cap;
+  uint32_t nrounds = P.nrounds;
+  bool final_pass = true;
+  bool fill = false;
+  const SegSlot* slots = nullptr;
+  if (P.blocks != nullptr) {
+    const SegBlock B = P.blocks[blockIdx.x];
+    blk = B.blk_in_seg;
+    log2cap = B.log2cap;
+    nrounds = B.nrounds;
+    final_pass = B.final_pass != 0;
+    fill = B.fill != 0;
+    slots = P.slots + B.first_slot;
+  }
+  const uint32_t gblk = blk << LOGT;
+  const uint32_t capmask = (1u << log2cap) - 1u;
+  const uint32_t merge_p = P.rounds[0].p;
+
+  K kr[E];
+  uint32_t vr[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) vr[r] = 0;
+
+  using SCHED = Schedule<LOGT, LOGE, MERGE>;
+  constexpr int NR = SCHED::count;
+
+  bool done = false;
+  static_for<0, NR>([&](auto I) {
+    constexpr SRound R = SCHED::value.r[decltype(I)::value];
+    constexpr int A = R.a;
+    if (done) return;
+    const uint32_t rd = uint32_t(decltype(I)::value);
+    const bool last = (rd + 1 == nrounds);
+    const bool from_global = (R.src == LOC_GLOBAL);
+    const bool to_global = last || (R.dst == LOC_GLOBAL);
+    const uint32_t tl = (tid & ((1u << A) - 1u)) | ((tid >> A) << (A + LOGE));
+    const uint32_t g_full = tl | gblk;
+    const uint32_t s_base = phys(tl);
+    uint32_t min_ = 0, mout = 0, g_t = g_full;
+    K* bk = gk;
+    uint32_t* bv = gv;
+    uint32_t seg_len = 0xFFFFFFFFu;
+    if (slots != nullptr && (from_global || to_global)) {
+      const SegSlot S = slots[g_full >> log2cap];
+      bk = gk + S.base;
+      if (V) bv = gv + S.base;
+      seg_len = S.len;
+      const uint32_t f = P.map_in | (S.desc ? kMapComplement : 0u);
+      if (rd == 0 && from_global) min_ = f;
+      if (last && final_pass) mout = f;
+      g_t = g_full & capmask;
+    } else {
+      if (rd == 0 && from_global) min_ = P.map_in;
+      if (last) mout = P.map_out;
+    }
+    const uint32_t g_dir = g_full & capmask;
+
+    if constexpr (R.kind == RK_PHASE_A) {
+      s_load<K, V, LOGE, 0, false>(kr, vr, true, bk, bv, g_t, sk, sv, s_base, min_, K(0));
+      if (fill) {
+        bool collide = false;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const uint32_t pos = g_t + uint32_t(r);
+          if (pos >= seg_len) {
+            kr[r] = ~K(0);
+            if (V) vr[r] = 0xFFFFFFFFu;
+          } else if (V && kr[r] == ~K(0)) {
+            collide = true;
+          }
+        }
+        if (collide && P.status != nullptr) atomicOr(P.status, int(kStatusSentinelCollision));
+      }
+      phase_a_small<K, V, LOGE>(kr, vr, log2cap);
+      if (uint32_t(LOGE) <= log2cap) {
+        const bool asc = ((g_dir & uint32_t(E) & capmask) == 0u);
+        if (VAR == kDivergent || !R.lanediv) {
+          if (asc)
+            window_side<K, V, LOGE, true>(kr, vr, LOGE);
+          else
+            window_side<K, V, LOGE, false>(kr, vr, LOGE);
+        } else {
+          const K m = asc ? K(0) : ~K(0);
+#pragma unroll
+          for (int r = 0; r < E; ++r) kr[r] ^= m;
+          window_side<K, V, LOGE, true>(kr, vr, LOGE);
+#pragma unroll
+          for (int r = 0; r < E; ++r) kr[r] ^= m;
+        }
+      }
+      s_store<K, V, LOGE, 0, false>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, K(0));
+    } else {
+      const uint32_t p = MERGE ? merge_p : uint32_t(R.p);
+      const bool asc = ((g_dir & (1u << p) & capmask) == 0u);
+      if (VAR == kDivergent || !R.lanediv) {
+        if (asc) {
+          s_load<K, V, LOGE, A, false>(kr, vr, from_global, bk, bv, g_t, sk, sv, s_base, min_, K(0));
+          window_side<K, V, LOGE, true>(kr, vr, R.cnt);
+          s_store<K, V, LOGE, A, false>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, K(0));
+        } else {
+          s_load<K, V, LOGE, A, true>(kr, vr, from_global, bk, bv, g_t, sk, sv, s_base, min_, K(0));
+          window_side<K, V, LOGE, false>(kr, vr, R.cnt);
+          s_store<K, V, LOGE, A, true>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, K(0));
+        }
+      } else {
+        const K m = asc ? K(0) : ~K(0);
+        s_load<K, V, LOGE, A, false>(kr, vr, from_global, bk, bv, g_t, sk, sv, s_base, min_, m);
+        window_side<K, V, LOGE, true>(kr, vr, R.cnt);
+        s_store<K, V, LOGE, A, false>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, m);
+      }
+    }
+    if (to_global) {
+      done = true;
+    } else {
+      __syncthreads();
+    }
+  });
+}
+
+}  // namespace darm

@@ -1,0 +1,70 @@
+// tile_u32.cu - compile-time-schedule tile and merge kernels for uint32_t keys.
+#include "kernel_table.h"
+#include "tile_kernel.cuh"
+
+namespace darm {
+namespace {
+
+template <bool V, int LOGE, int LOGT, int VAR, bool MERGE>
+KernelEntry tentry() {
+  constexpr int MT = max_threads_for<uint32_t, V, LOGE>();
+  static_assert((1 << (LOGT - LOGE)) <= MT, "tile too large for the block size");
+  return KernelEntry{
+      reinterpret_cast<const void*>(&darm_tile_kernel<uint32_t, V, LOGE, LOGT, VAR, MERGE, MT>), MT};
+}
+
+template <bool V, int LOGE, int LOGT>
+KernelEntry tpick(int var, bool merge) {
+  if (merge) return var ? tentry<V, LOGE, LOGT, 1, true>() : tentry<V, LOGE, LOGT, 0, true>();
+  return var ? tentry<V, LOGE, LOGT, 1, false>() : tentry<V, LOGE, LOGT, 0, false>();
+}
+
+struct Combo {
+  bool v;
+  int loge, logt;
+};
+constexpr Combo kCombos[] = {{false, 4, 12}, {false, 4, 13}, {false, 4, 14}, {true, 4, 12}, {true, 4, 13}};
+
+}  // namespace
+
+KernelEntry tile_kernel_u32(bool has_vals, int loge, int logt, int var, bool merge) {
+  if (!has_vals && loge == 4 && logt == 12) return tpick<false, 4, 12>(var, merge);
+  if (!has_vals && loge == 4 && logt == 13) return tpick<false, 4, 13>(var, merge);
+  if (!has_vals && loge == 4 && logt == 14) return tpick<false, 4, 14>(var, merge);
+  if (has_vals && loge == 4 && logt == 12) return tpick<true, 4, 12>(var, merge);
+  if (has_vals && loge == 4 && logt == 13) return tpick<true, 4, 13>(var, merge);
+  return KernelEntry{nullptr, 0};
+}
+
+void for_each_tile_kernel_u32(void (*fn)(const void*, void*), void* ctx) {
+  for (const Combo& c : kCombos)
+    for (int var = 0; var < 2; ++var)
+      for (int merge = 0; merge < 2; ++merge) {
+        KernelEntry e = tile_kernel_u32(c.v, c.loge, c.logt, var, merge != 0);
+        if (e.fn) fn(e.fn, ctx);
+      }
+}
+
+// The compile-time schedules, exported so that the planner can check them
+// against its own round lists.
+int fixed_schedule_rounds(int logt, int loge, bool merge, SRound* out, int cap) {
+  auto copy = [&](const auto& sch, int n) {
+    for (int i = 0; i < n && i < cap; ++i) out[i] = sch.r[i];
+    return n;
+  };
+  if (loge == 4 && logt == 12)
+    return merge ? copy(Schedule<12, 4, true>::value, Schedule<12, 4, true>::count)
+                 : copy(Schedule<12, 4, false>::value, Schedule<12, 4, false>::count);
+  if (loge == 4 && logt == 13)
+    return merge ? copy(Schedule<13, 4, true>::value, Schedule<13, 4, true>::count)
+                 : copy(Schedule<13, 4, false>::value, Schedule<13, 4, false>::count);
+  if (loge == 4 && logt == 14)
+    return merge ? copy(Schedule<14, 4, true>::value, Schedule<14, 4, true>::count)
+                 : copy(Schedule<14, 4, false>::value, Schedule<14, 4, false>::count);
+  if (loge == 3 && logt == 12)
+    return merge ? copy(Schedule<12, 3, true>::value, Schedule<12, 3, true>::count)
+                 : copy(Schedule<12, 3, false>::value, Schedule<12, 3, false>::count);
+  return -1;
+}
+
+}  // namespace darm
