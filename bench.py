@@ -34,7 +34,7 @@ L2_FLUSH_BYTES = 256 << 20  # larger than the 126 MiB L2
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["darm", "reference"], default="darm")
     ap.add_argument("--workload", choices=["kv24", "kv24skew", "f32"], default="kv24")
@@ -75,7 +75,7 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -268,6 +268,7 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
+    time.sleep(1.0)  # let the sampler start before the timed region
     ms_meld, launches_meld = timed_steps("melded", args.steps, args.warmup)
     ms_div, launches_div = timed_steps("divergent", args.steps, args.warmup)
     clk = clocks.stop()

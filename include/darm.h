@@ -119,8 +119,8 @@ int darm_bitonic_sort_host(void* keys, uint32_t* vals, size_t n, int dtype,
 
 /* Sort num_segs independent segments in one batched launch sequence.
  * Segment s occupies elements [seg_offsets[s], seg_offsets[s+1]) of keys
- * and vals; its capacity (the difference) must be a power of two and the
- * offsets a multiple of 4 elements.  Only the first seg_len[s] elements are
+ * and vals; its capacity (the difference) must be a power of two and its
+ * offset a multiple of min(capacity, 4) elements.  Only the first seg_len[s] elements are
  * real: the library writes the sentinel (UINT32_MAX for ascending, 0 for
  * descending; payload 0xFFFFFFFF) beyond them and sorts the whole capacity,
  * so the real keys end up first.  seg_offsets (uint64, num_segs + 1

@@ -33,7 +33,7 @@ const void* fixed_kernel_fn(KeyKind kk, bool has_vals, int loge, int logt, int v
 }
 
 int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_t* vals,
-                cudaStream_t stream) {
+                cudaStream_t stream, bool count) {
   const bool has_vals = vals != nullptr;
   for (const Launch& L : plan) {
     PassParams P = L.P;
@@ -50,7 +50,7 @@ int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_
       fprintf(stderr, "darm: launch failed: %s\n", cudaGetErrorString(err));
       return DARM_ERR_CUDA;
     }
-    g_ctx.launches.fetch_add(1, std::memory_order_relaxed);
+    if (count) g_ctx.launches.fetch_add(1, std::memory_order_relaxed);
   }
   return DARM_OK;
 }
@@ -107,9 +107,17 @@ int sort_device(KeyKind kk, bool f32, void* keys, uint32_t* vals, size_t n, int 
   return launch_plan(*plan, kk, keys, vals, stream);
 }
 
+// Allow each kernel the device's opt-in shared memory minus what it
+// declares statically.
 static void set_smem_attr(const void* fn, void* ctx) {
-  const int bytes = *static_cast<int*>(ctx);
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  int* st = static_cast<int*>(ctx);  // {opt-in bytes, first error}
+  cudaFuncAttributes fa;
+  cudaError_t err = cudaFuncGetAttributes(&fa, fn);
+  if (err == cudaSuccess) {
+    const int bytes = st[0] - int(fa.sharedSizeBytes);
+    err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  }
+  if (err != cudaSuccess && st[1] == 0) st[1] = int(err);
 }
 
 }  // namespace darm
@@ -131,10 +139,18 @@ int darm_sort_init(int device, size_t workspace_bytes) {
   g_ctx.device = device;
   g_ctx.sms = sms;
   g_ctx.smem_limit = size_t(optin);
-  for_each_kernel_u32(set_smem_attr, &optin);
-  for_each_kernel_u64(set_smem_attr, &optin);
-  for_each_tile_kernel_u32(set_smem_attr, &optin);
-  for_each_tile_kernel_u64(set_smem_attr, &optin);
+  int st[2] = {optin, 0};
+  for_each_kernel_u32(set_smem_attr, st);
+  for_each_kernel_u64(set_smem_attr, st);
+  for_each_tile_kernel_u32(set_smem_attr, st);
+  for_each_tile_kernel_u64(set_smem_attr, st);
+  if (st[1] != 0) {
+    fprintf(stderr, "darm: configuring shared memory failed: %s\n",
+            cudaGetErrorString(cudaError_t(st[1])));
+    cudaGetLastError();
+    return DARM_ERR_CUDA;
+  }
+  g_ctx.smem_limit = size_t(optin) - 64;  // room for the kernels' static shared memory
   if (cudaMalloc(&g_ctx.d_status, sizeof(int)) != cudaSuccess) return DARM_ERR_OOM;
   if (cudaMemset(g_ctx.d_status, 0, sizeof(int)) != cudaSuccess) return DARM_ERR_CUDA;
   if (cudaStreamCreateWithFlags(&g_ctx.host_stream, cudaStreamNonBlocking) != cudaSuccess)

@@ -37,8 +37,11 @@ extern Context g_ctx;
 
 const void* kernel_fn(KeyKind kk, bool has_vals, int loge, int variant);
 const void* fixed_kernel_fn(KeyKind kk, bool has_vals, int loge, int logt, int variant, bool merge);
+// Enqueue every launch of `plan` on `stream`; `count` adds them to the
+// library's launch counter (off while capturing a graph, whose replays are
+// counted instead).
 int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_t* vals,
-                cudaStream_t stream);
+                cudaStream_t stream, bool count = true);
 Tuning tuning_for(KeyKind kk, bool has_vals, int m);
 const std::vector<Launch>* cached_plan(KeyKind kk, bool has_vals, int m, int variant,
                                        uint32_t map_in, uint32_t map_out);

@@ -55,7 +55,7 @@ enum RoundKind : uint8_t {
   RK_PHASE_A = 0,  // register sort of E consecutive elements, stages k <= E
   RK_WINDOW = 1    // layers of one stage k on the window bits a..a+LOGE-1
 };
-enum Loc : uint8_t { LOC_GLOBAL = 0, LOC_SMEM = 1 };
+enum Loc : uint8_t { LOC_GLOBAL = 0, LOC_SMEM = 1, LOC_NONE = 2 /* unused slot: no access */ };
 
 struct Round {
   uint8_t kind;  // RoundKind
@@ -78,8 +78,10 @@ constexpr uint32_t kMapComplement = 2u;  // descending: x -> ~x
 struct SegSlot {
   uint64_t base;   // first element of the segment
   uint32_t len;    // real elements (positions >= len get the sentinel)
-  uint32_t desc;   // 1: this segment sorts descending
+  uint32_t flags;  // kSlotDesc | kSlotEmpty
 };
+constexpr uint32_t kSlotDesc = 1u;   // this segment sorts descending
+constexpr uint32_t kSlotEmpty = 2u;  // unused slot of a packed block: no memory access
 // One entry per launched block.  A block either covers part of one segment
 // (blk_in_seg numbers the blocks of that segment) or, when the segment is
 // smaller than the block, 2^(b - log2cap) whole segments stored in
@@ -90,7 +92,8 @@ struct SegBlock {
   uint8_t log2cap;
   uint8_t nrounds;     // rounds this block runs (small segments stop early)
   uint8_t final_pass;  // this pass completes the segment: undo key maps
-  uint8_t fill;        // first load writes sentinels beyond len
+  uint8_t fill;        // first pass: apply the segment's key map and write
+                       // sentinels beyond len
 };
 
 constexpr uint32_t kStatusSentinelCollision = 8u;  // == DARM_ERR_SENTINEL_COLLISION
@@ -107,6 +110,9 @@ struct PassParams {
   const SegBlock* blocks;  // segmented passes: per-block table, else nullptr
   const SegSlot* slots;
   int* status;             // device status word (sentinel collisions)
+  unsigned int* work_counter;  // persistent launches: next block to take
+  uint32_t nblocks;            // persistent launches: blocks in the table
+  uint32_t pad2;
   Round rounds[kMaxRounds];
 };
 
@@ -221,6 +227,14 @@ __device__ __forceinline__ void load_elems(K (&kr)[1 << LOGE], uint32_t (&vr)[1 
                                            const K* sk, const uint32_t* sv, uint32_t mapf, K m) {
   constexpr int E = 1 << LOGE;
   constexpr int KPV = 16 / sizeof(K);  // keys per 16-byte vector
+  if (src == LOC_NONE) {
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      kr[r] = K(0);
+      vr[r] = 0u;
+    }
+    return;
+  }
   if (src == LOC_GLOBAL) {
     if (vec && E >= KPV) {
 #pragma unroll
@@ -315,6 +329,7 @@ __device__ __forceinline__ void store_elems(const K (&kr)[1 << LOGE], const uint
                                             K* sk, uint32_t* sv, uint32_t mapf, K m) {
   constexpr int E = 1 << LOGE;
   constexpr int KPV = 16 / sizeof(K);
+  if (dst == LOC_NONE) return;
   if (dst == LOC_GLOBAL) {
     if (vec && E >= KPV) {
 #pragma unroll
@@ -515,14 +530,16 @@ __global__ void __launch_bounds__(MAXT, 1) darm_pass_kernel(const __grid_constan
     K* bk = gk;
     uint32_t* bv = gv;
     uint32_t seg_len = 0xFFFFFFFFu;
+    bool skip_mem = false;
     if (slots != nullptr && (src == LOC_GLOBAL || dst == LOC_GLOBAL)) {
       // all E elements of this thread lie in one segment (E <= cap)
       const SegSlot S = slots[g_full >> log2cap];
       bk = gk + S.base;
       if (V) bv = gv + S.base;
       seg_len = S.len;
-      const uint32_t f = P.map_in | (S.desc ? kMapComplement : 0u);
-      if (rd == 0 && src == LOC_GLOBAL) min_ = f;
+      skip_mem = (S.flags & kSlotEmpty) != 0;
+      const uint32_t f = P.map_in | ((S.flags & kSlotDesc) ? kMapComplement : 0u);
+      if (rd == 0 && src == LOC_GLOBAL && fill) min_ = f;
       if (last && final_pass) mout = f;
       A.g_t = g_full & capmask;
     } else {
@@ -530,6 +547,8 @@ __global__ void __launch_bounds__(MAXT, 1) darm_pass_kernel(const __grid_constan
       if (rd == 0 && src == LOC_GLOBAL) min_ = P.map_in;
       if (last) mout = P.map_out;
     }
+    const uint8_t src_e = (skip_mem && src == LOC_GLOBAL) ? uint8_t(LOC_NONE) : src;
+    const uint8_t dst_e = (skip_mem && dst == LOC_GLOBAL) ? uint8_t(LOC_NONE) : dst;
     // direction bits are read from the index within the segment
     const uint32_t g_dir = g_full & capmask;
     // the planner marks rounds whose direction can differ between the
@@ -537,7 +556,7 @@ __global__ void __launch_bounds__(MAXT, 1) darm_pass_kernel(const __grid_constan
     const bool lane_divergent = R.lanediv != 0;
 
     if (R.kind == RK_PHASE_A) {
-      load_elems<K, V, LOGE, false>(kr, vr, src, vec, A, bk, bv, sk, sv, min_, K(0));
+      load_elems<K, V, LOGE, false>(kr, vr, src_e, vec, A, bk, bv, sk, sv, min_, K(0));
       if (fill) {
         // segment padding: positions at or beyond the real length take the
         // largest key; a real key equal to it is a collision when a payload
@@ -573,20 +592,20 @@ __global__ void __launch_bounds__(MAXT, 1) darm_pass_kernel(const __grid_constan
           for (int r = 0; r < E; ++r) kr[r] ^= m;
         }
       }
-      store_elems<K, V, LOGE, false>(kr, vr, dst, vec, A, bk, bv, sk, sv, mout, K(0));
+      store_elems<K, V, LOGE, false>(kr, vr, dst_e, vec, A, bk, bv, sk, sv, mout, K(0));
     } else {
       const bool asc = ((g_dir & (1u << R.p) & capmask) == 0u);
       const int cnt = R.cnt;
       if (VAR == kDivergent || !lane_divergent) {
         // Fig. 1: one full copy of the body per direction
         if (asc) {
-          load_elems<K, V, LOGE, false>(kr, vr, src, vec, A, bk, bv, sk, sv, min_, K(0));
+          load_elems<K, V, LOGE, false>(kr, vr, src_e, vec, A, bk, bv, sk, sv, min_, K(0));
           window_side<K, V, LOGE, true>(kr, vr, cnt);
-          store_elems<K, V, LOGE, false>(kr, vr, dst, vec, A, bk, bv, sk, sv, mout, K(0));
+          store_elems<K, V, LOGE, false>(kr, vr, dst_e, vec, A, bk, bv, sk, sv, mout, K(0));
         } else {
-          load_elems<K, V, LOGE, true>(kr, vr, src, vec, A, bk, bv, sk, sv, min_, K(0));
+          load_elems<K, V, LOGE, true>(kr, vr, src_e, vec, A, bk, bv, sk, sv, min_, K(0));
           window_side<K, V, LOGE, false>(kr, vr, cnt);
-          store_elems<K, V, LOGE, true>(kr, vr, dst, vec, A, bk, bv, sk, sv, mout, K(0));
+          store_elems<K, V, LOGE, true>(kr, vr, dst_e, vec, A, bk, bv, sk, sv, mout, K(0));
         }
       } else {
         // melded: one copy of the loads, compares and stores.  The two sides'
@@ -595,9 +614,9 @@ __global__ void __launch_bounds__(MAXT, 1) darm_pass_kernel(const __grid_constan
         // complemented (x -> ~x reverses unsigned order), so both sides run
         // the same ascending compare-exchange, and the stores undo it.
         const K m = asc ? K(0) : ~K(0);
-        load_elems<K, V, LOGE, false>(kr, vr, src, vec, A, bk, bv, sk, sv, min_, m);
+        load_elems<K, V, LOGE, false>(kr, vr, src_e, vec, A, bk, bv, sk, sv, min_, m);
         window_side<K, V, LOGE, true>(kr, vr, cnt);
-        store_elems<K, V, LOGE, false>(kr, vr, dst, vec, A, bk, bv, sk, sv, mout, m);
+        store_elems<K, V, LOGE, false>(kr, vr, dst_e, vec, A, bk, bv, sk, sv, mout, m);
       }
     }
     if (dst == LOC_SMEM) __syncthreads();

@@ -266,26 +266,23 @@ __device__ __forceinline__ void s_store(const K (&kr)[1 << LOGE], const uint32_t
   }
 }
 
-template <typename K, bool V, int LOGE, int LOGT, int VAR, bool MERGE, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) darm_tile_kernel(const __grid_constant__ PassParams P) {
+// One block of a tile or merge pass.  `bidx` is the block number, or the
+// entry of the segmented block table.
+template <typename K, bool V, int LOGE, int LOGT, int VAR, bool MERGE>
+__device__ __forceinline__ void tile_block(const PassParams& P, uint32_t bidx, K* sk, uint32_t* sv) {
   constexpr int E = 1 << LOGE;
-  constexpr uint32_t SW = smem_words(1u << LOGT);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  K* sk = reinterpret_cast<K*>(smem_raw);
-  uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + sizeof(K) * SW);
-
   K* __restrict__ gk = reinterpret_cast<K*>(P.keys);
   uint32_t* __restrict__ gv = P.vals;
   const uint32_t tid = threadIdx.x;
 
-  uint32_t blk = blockIdx.x;
+  uint32_t blk = bidx;
   uint32_t log2cap = P.log2cap;
   uint32_t nrounds = P.nrounds;
   bool final_pass = true;
   bool fill = false;
   const SegSlot* slots = nullptr;
   if (P.blocks != nullptr) {
-    const SegBlock B = P.blocks[blockIdx.x];
+    const SegBlock B = P.blocks[bidx];
     blk = B.blk_in_seg;
     log2cap = B.log2cap;
     nrounds = B.nrounds;
@@ -321,13 +318,15 @@ __global__ void __launch_bounds__(MAXT, 1) darm_tile_kernel(const __grid_constan
     K* bk = gk;
     uint32_t* bv = gv;
     uint32_t seg_len = 0xFFFFFFFFu;
+    bool skip = false;  // unused slot of a packed block: touch no memory
     if (slots != nullptr && (from_global || to_global)) {
       const SegSlot S = slots[g_full >> log2cap];
       bk = gk + S.base;
       if (V) bv = gv + S.base;
       seg_len = S.len;
-      const uint32_t f = P.map_in | (S.desc ? kMapComplement : 0u);
-      if (rd == 0 && from_global) min_ = f;
+      skip = (S.flags & kSlotEmpty) != 0;
+      const uint32_t f = P.map_in | ((S.flags & kSlotDesc) ? kMapComplement : 0u);
+      if (rd == 0 && from_global && fill) min_ = f;
       if (last && final_pass) mout = f;
       g_t = g_full & capmask;
     } else {
@@ -335,9 +334,10 @@ __global__ void __launch_bounds__(MAXT, 1) darm_tile_kernel(const __grid_constan
       if (last) mout = P.map_out;
     }
     const uint32_t g_dir = g_full & capmask;
+    const bool do_store = !(to_global && skip);
 
     if constexpr (R.kind == RK_PHASE_A) {
-      s_load<K, V, LOGE, 0, false>(kr, vr, true, bk, bv, g_t, sk, sv, s_base, min_, K(0));
+      if (!skip) s_load<K, V, LOGE, 0, false>(kr, vr, true, bk, bv, g_t, sk, sv, s_base, min_, K(0));
       if (fill) {
         bool collide = false;
 #pragma unroll
@@ -350,7 +350,8 @@ __global__ void __launch_bounds__(MAXT, 1) darm_tile_kernel(const __grid_constan
             collide = true;
           }
         }
-        if (collide && P.status != nullptr) atomicOr(P.status, int(kStatusSentinelCollision));
+        if (collide && !skip && P.status != nullptr)
+          atomicOr(P.status, int(kStatusSentinelCollision));
       }
       phase_a_small<K, V, LOGE>(kr, vr, log2cap);
       if (uint32_t(LOGE) <= log2cap) {
@@ -369,25 +370,31 @@ __global__ void __launch_bounds__(MAXT, 1) darm_tile_kernel(const __grid_constan
           for (int r = 0; r < E; ++r) kr[r] ^= m;
         }
       }
-      s_store<K, V, LOGE, 0, false>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, K(0));
+      if (do_store)
+        s_store<K, V, LOGE, 0, false>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, K(0));
     } else {
       const uint32_t p = MERGE ? merge_p : uint32_t(R.p);
       const bool asc = ((g_dir & (1u << p) & capmask) == 0u);
       if (VAR == kDivergent || !R.lanediv) {
+        // Fig. 1: one full copy of the body per direction
         if (asc) {
           s_load<K, V, LOGE, A, false>(kr, vr, from_global, bk, bv, g_t, sk, sv, s_base, min_, K(0));
           window_side<K, V, LOGE, true>(kr, vr, R.cnt);
-          s_store<K, V, LOGE, A, false>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, K(0));
+          if (do_store)
+            s_store<K, V, LOGE, A, false>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, K(0));
         } else {
           s_load<K, V, LOGE, A, true>(kr, vr, from_global, bk, bv, g_t, sk, sv, s_base, min_, K(0));
           window_side<K, V, LOGE, false>(kr, vr, R.cnt);
-          s_store<K, V, LOGE, A, true>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, K(0));
+          if (do_store)
+            s_store<K, V, LOGE, A, true>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, K(0));
         }
       } else {
+        // melded: one copy; the descending side's keys enter complemented
         const K m = asc ? K(0) : ~K(0);
         s_load<K, V, LOGE, A, false>(kr, vr, from_global, bk, bv, g_t, sk, sv, s_base, min_, m);
         window_side<K, V, LOGE, true>(kr, vr, R.cnt);
-        s_store<K, V, LOGE, A, false>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, m);
+        if (do_store)
+          s_store<K, V, LOGE, A, false>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, m);
       }
     }
     if (to_global) {
@@ -396,6 +403,29 @@ __global__ void __launch_bounds__(MAXT, 1) darm_tile_kernel(const __grid_constan
       __syncthreads();
     }
   });
+}
+
+template <typename K, bool V, int LOGE, int LOGT, int VAR, bool MERGE, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) darm_tile_kernel(const __grid_constant__ PassParams P) {
+  constexpr uint32_t SW = smem_words(1u << LOGT);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  K* sk = reinterpret_cast<K*>(smem_raw);
+  uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + sizeof(K) * SW);
+  if (P.work_counter == nullptr) {
+    tile_block<K, V, LOGE, LOGT, VAR, MERGE>(P, blockIdx.x, sk, sv);
+    return;
+  }
+  // persistent: blocks of the table (longest segments first) are taken in
+  // order from a global counter as CTAs become free
+  __shared__ uint32_t s_next;
+  for (;;) {
+    if (threadIdx.x == 0) s_next = atomicAdd(P.work_counter, 1u);
+    __syncthreads();
+    const uint32_t b = s_next;
+    __syncthreads();
+    if (b >= P.nblocks) break;
+    tile_block<K, V, LOGE, LOGT, VAR, MERGE>(P, b, sk, sv);
+  }
 }
 
 }  // namespace darm

@@ -33,12 +33,22 @@ SEED_CFG5 = 0xDA2C0005
 
 def splitmix64(seed: int, count: int, start: int = 0) -> np.ndarray:
     """Outputs start .. start+count-1 of the SplitMix64 stream `seed` (uint64)."""
+    out = np.empty(count, dtype=np.uint64)
+    chunk = 1 << 20
+    s0 = np.uint64(seed & 0xFFFFFFFFFFFFFFFF)
     with np.errstate(over="ignore"):
-        ctr = np.arange(start + 1, start + count + 1, dtype=np.uint64)
-        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + ctr * GAMMA
-        z = (z ^ (z >> np.uint64(30))) * _M1
-        z = (z ^ (z >> np.uint64(27))) * _M2
-        return z ^ (z >> np.uint64(31))
+        for lo in range(0, count, chunk):
+            hi = min(count, lo + chunk)
+            z = np.arange(start + lo + 1, start + hi + 1, dtype=np.uint64)
+            z *= GAMMA
+            z += s0
+            z ^= z >> np.uint64(30)
+            z *= _M1
+            z ^= z >> np.uint64(27)
+            z *= _M2
+            z ^= z >> np.uint64(31)
+            out[lo:hi] = z
+    return out
 
 
 def substream(seed: int, tag: int) -> int:
@@ -147,25 +157,28 @@ def next_pow2(x: np.ndarray) -> np.ndarray:
 
 def cfg4_segments(seed: int = SEED_CFG4, num_segments: int = 10000,
                   min_len: int = 32, max_len: int = 65536,
-                  mixed_dirs: bool = False) -> Segments:
+                  mixed_dirs: bool = False, largest_first: bool = False) -> Segments:
     """Independent uint32 arrays with log-uniform real lengths in
     [min_len, max_len], each stored at the next power-of-two capacity,
-    laid out back to back.  Keys are uniform in [0, 2^32 - 1) so that no real
-    key equals the ascending sentinel; payload = index within the segment."""
+    laid out back to back (largest capacity first when `largest_first`, which
+    puts every segment at a multiple of its capacity).  Keys are uniform in
+    [0, 2^32 - 1) so that no real key equals the ascending sentinel; payload =
+    index within the segment."""
     u = uniform01(substream(seed, 1), num_segments)
     lo, hi = math.log(min_len), math.log(max_len)
     lens = np.floor(np.exp(lo + (hi - lo) * u)).astype(np.int64)
     lens = np.clip(lens, min_len, max_len)
     caps = next_pow2(lens)
+    if largest_first:
+        order = np.argsort(-caps, kind="stable")
+        lens, caps = lens[order], caps[order]
     offsets = np.zeros(num_segments + 1, dtype=np.uint64)
     offsets[1:] = np.cumsum(caps).astype(np.uint64)
     total = int(offsets[-1])
     w = uniform_u32(substream(seed, 2), total).astype(np.uint64)
     keys = ((w * np.uint64(0xFFFFFFFF)) >> np.uint64(32)).astype(np.uint32)
-    vals = np.empty(total, dtype=np.uint32)
-    for s in range(num_segments):
-        a, c = int(offsets[s]), int(caps[s])
-        vals[a:a + c] = np.arange(c, dtype=np.uint32)
+    vals = (np.arange(total, dtype=np.int64)
+            - np.repeat(offsets[:-1].astype(np.int64), caps)).astype(np.uint32)
     if mixed_dirs:
         desc = (uniform_u32(substream(seed, 3), num_segments) & np.uint32(1)).astype(np.uint8)
     else:
