@@ -199,6 +199,12 @@ int darm_sort_serve_wait(uint64_t req_id, int timeout_ms);
 int darm_sort_serve_stats(double* p50_ms, double* p99_ms, double* keys_per_s,
                           uint64_t* completed);
 
+/* Fault injection for tests: the next tick's launches fail with `status`
+ * (on the host, before anything is launched); every job that tick carried
+ * completes with that status and its arena space is released.  No device
+ * fault is involved. */
+int darm_sort_serve_inject_fault(int status);
+
 /* Drain outstanding jobs, stop the scheduler and free the arena. */
 int darm_sort_serve_stop(void);
 

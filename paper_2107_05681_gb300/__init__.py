@@ -71,6 +71,7 @@ _sig = {
     "darm_sort_serve_stats": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u64)], _i32),
     "darm_sort_serve_stop": ([], _i32),
+    "darm_sort_serve_inject_fault": ([_i32], _i32),
 }
 for _name, (_args, _res) in _sig.items():
     _fn = getattr(lib, _name)
@@ -239,3 +240,59 @@ def autotune(dtype: int, n: int, has_vals: bool, db_path: str | None = None) -> 
 
 def load_tune_db(db_path: str) -> None:
     _check(lib.darm_load_tune_db(db_path.encode()), "darm_load_tune_db")
+
+
+# ---- serving -----------------------------------------------------------------
+
+def serve_start(budget_bytes: int, max_inflight: int = 64, variant="melded",
+                num_streams: int = 1) -> None:
+    """Start the continuous-batching scheduler with a device arena of
+    `budget_bytes` (a job of n keys costs 12 * next_pow2(n) bytes)."""
+    cfg = ServeCfg(int(budget_bytes), int(max_inflight), _variant(variant), int(num_streams))
+    _check(lib.darm_sort_serve_start(ctypes.byref(cfg)), "darm_sort_serve_start")
+
+
+def serve_submit(keys, vals=None, descending: bool = False) -> int:
+    """Queue an in-place sort of a CUDA tensor (uint64, uint32 or float32
+    keys; optional uint32 payload).  The tensors must stay alive until done."""
+    import torch
+    dt = {torch.uint32: U32, torch.float32: F32, torch.uint64: U64}.get(keys.dtype)
+    if dt is None or not keys.is_cuda or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous uint64/uint32/float32 CUDA tensor")
+    vp = None
+    if vals is not None:
+        if vals.dtype != torch.uint32 or vals.shape != keys.shape or not vals.is_contiguous():
+            raise ValueError("vals must be a contiguous uint32 CUDA tensor shaped like keys")
+        vp = ctypes.c_void_p(vals.data_ptr())
+    rid = _u64(0)
+    _check(lib.darm_sort_serve_submit(ctypes.c_void_p(keys.data_ptr()), vp, keys.numel(), dt,
+                                      DESC if descending else ASC, ctypes.byref(rid)),
+           "darm_sort_serve_submit")
+    return int(rid.value)
+
+
+def serve_poll(req_id: int) -> bool:
+    done = _i32(0)
+    _check(lib.darm_sort_serve_poll(int(req_id), ctypes.byref(done)), "darm_sort_serve_poll")
+    return bool(done.value)
+
+
+def serve_wait(req_id: int, timeout_ms: int = 60000) -> None:
+    _check(lib.darm_sort_serve_wait(int(req_id), int(timeout_ms)), "darm_sort_serve_wait")
+
+
+def serve_stats():
+    """(p50 ms, p99 ms, keys/s, completed) over all completed requests."""
+    p50, p99, kps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    done = _u64(0)
+    _check(lib.darm_sort_serve_stats(ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(kps),
+                                     ctypes.byref(done)), "darm_sort_serve_stats")
+    return p50.value, p99.value, kps.value, int(done.value)
+
+
+def serve_inject_fault(status: int) -> None:
+    _check(lib.darm_sort_serve_inject_fault(int(status)), "darm_sort_serve_inject_fault")
+
+
+def serve_stop() -> None:
+    _check(lib.darm_sort_serve_stop(), "darm_sort_serve_stop")

@@ -32,6 +32,7 @@
 #include "darm_internal.h"
 #include "kernel_table.h"
 #include "plan.h"
+#include "batch.h"
 #include "tile_kernel.cuh"
 
 namespace darm {
@@ -82,204 +83,41 @@ int log2u(uint64_t v) {
   return m;
 }
 
-// Index of the round after which a tile-schedule block whose segments have
-// capacity 2^c is complete (the bottom window of stage c).
-int rounds_through(int c, int e) {
-  int n = 1;
-  for (int p = e + 1; p <= c; ++p) n += (p + e - 1) / e;
-  return n;
-}
-
-int occupancy_grid(const void* fn, int threads, size_t smem) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  return per_sm * std::max(1, g_ctx.sms);
-}
-
-struct SegInfo {
-  uint32_t idx;
-  uint64_t base;
-  uint32_t len;
-  int c;
-  bool desc;
-};
-
 // Build the launch list, device tables and graph for one layout.
-int build_seg_plan(SegPlan& sp, uint32_t* keys, uint32_t* vals, const std::vector<SegInfo>& segs,
+int build_seg_plan(SegPlan& sp, uint32_t* keys, uint32_t* vals, const std::vector<BatchSeg>& segs,
                    int variant) {
   const bool has_vals = vals != nullptr;
   const KeyKind kk = KEY_U32;
-  Tuning tn = tuning_for(kk, has_vals, 0);
   int cmax = 0;
-  for (const SegInfo& s : segs) cmax = std::max(cmax, s.c);
-  if (!fit_tuning(tn, kk, has_vals, std::max(cmax, tn.t), g_ctx.smem_limit)) return DARM_ERR_INVALID_ARG;
-  const int t = tn.t, e = tn.e1;
-  const size_t tile_smem = size_t(elem_bytes(kk, has_vals)) * smem_words(1u << t);
-
-  // --- tables -------------------------------------------------------------
-  std::vector<SegSlot> slots;
-  std::vector<SegBlock> blocks;
-  std::vector<const SegInfo*> order;
-  for (const SegInfo& s : segs)
-    if (s.c >= e) order.push_back(&s);
-  std::stable_sort(order.begin(), order.end(),
-                   [](const SegInfo* a, const SegInfo* b) { return a->c > b->c; });
-  std::vector<uint32_t> slot_of(segs.size(), 0xFFFFFFFFu);
-  auto add_slot = [&](const SegInfo& s) {
-    SegSlot sl{};
-    sl.base = s.base;
-    sl.len = s.len;
-    sl.flags = s.desc ? kSlotDesc : 0u;
-    slots.push_back(sl);
-    return uint32_t(slots.size() - 1);
-  };
-
-  // tile pass blocks, longest first
-  const int nr_full = rounds_through(t, e);
-  size_t i = 0;
-  while (i < order.size()) {
-    const int c = order[i]->c;
-    if (c >= t) {
-      const SegInfo& s = *order[i];
-      const uint32_t sl = add_slot(s);
-      slot_of[&s - &segs[0]] = sl;
-      for (uint32_t b = 0; b < (1u << (c - t)); ++b) {
-        SegBlock B{};
-        B.first_slot = sl;
-        B.blk_in_seg = b;
-        B.log2cap = uint8_t(c);
-        B.nrounds = uint8_t(nr_full);
-        B.final_pass = (c == t) ? 1 : 0;
-        B.fill = 1;
-        blocks.push_back(B);
-      }
-      ++i;
-    } else {
-      // pack 2^(t-c) segments of this class per block
-      const uint32_t per = 1u << (t - c);
-      const uint32_t first = uint32_t(slots.size());
-      uint32_t taken = 0;
-      while (i < order.size() && order[i]->c == c && taken < per) {
-        add_slot(*order[i]);
-        ++taken;
-        ++i;
-      }
-      for (; taken < per; ++taken) {
-        SegSlot empty{};
-        empty.flags = kSlotEmpty;
-        slots.push_back(empty);
-      }
-      SegBlock B{};
-      B.first_slot = first;
-      B.blk_in_seg = 0;
-      B.log2cap = uint8_t(c);
-      B.nrounds = uint8_t(rounds_through(c, e));
-      B.final_pass = 1;
-      B.fill = 1;
-      blocks.push_back(B);
-    }
-  }
-  const uint32_t tile_blocks = uint32_t(blocks.size());
-
-  // tiny segments (capacity 2..2^(e-1)): one thread per segment, Phase A only
-  struct TinyLaunch {
-    int c;
-    uint32_t first_block, nblocks;
-  };
-  std::vector<TinyLaunch> tiny;
-  const int tiny_threads_log2 = 7;
-  for (int c = e - 1; c >= 1; --c) {
-    std::vector<const SegInfo*> cls;
-    for (const SegInfo& s : segs)
-      if (s.c == c) cls.push_back(&s);
-    if (cls.empty()) continue;
-    const uint32_t per = 1u << tiny_threads_log2;
-    TinyLaunch tl{c, uint32_t(blocks.size()), 0};
-    for (size_t j = 0; j < cls.size(); j += per) {
-      const uint32_t first = uint32_t(slots.size());
-      for (size_t q = 0; q < per; ++q) {
-        if (j + q < cls.size()) {
-          add_slot(*cls[j + q]);
-        } else {
-          SegSlot empty{};
-          empty.flags = kSlotEmpty;
-          slots.push_back(empty);
-        }
-      }
-      SegBlock B{};
-      B.first_slot = first;
-      B.log2cap = uint8_t(c);
-      B.nrounds = 1;
-      B.final_pass = 1;
-      B.fill = 1;
-      blocks.push_back(B);
-      ++tl.nblocks;
-    }
-    tiny.push_back(tl);
-  }
-
-  // passes for segments larger than a tile
-  struct BigLaunch {
-    Launch L;
-    uint32_t first_block, nblocks;
-  };
-  std::vector<BigLaunch> big;
-  for (int p = t + 1; p <= cmax; ++p) {
-    std::vector<const SegInfo*> act;
-    for (const SegInfo* s : order)
-      if (s->c >= p) act.push_back(s);
-    if (act.empty()) break;
-    // window passes: one plan_array stage gives the shapes; copy them
-    std::vector<Launch> shape;
-    plan_array(shape, kk, has_vals, p, tn, variant, 0, 0, g_ctx.smem_limit);
-    // the launches of stage p are the ones after the stage p-1 merge pass:
-    // take every window pass with rounds at stage p, and the final merge
-    for (const Launch& L0 : shape) {
-      if (L0.kind == PASS_TILE) continue;
-      if (L0.P.rounds[0].p != p) continue;
-      BigLaunch bl;
-      bl.L = L0;
-      bl.first_block = uint32_t(blocks.size());
-      const uint32_t bsize_log2 = L0.P.b;
-      for (const SegInfo* s : act) {
-        const uint32_t sl = slot_of[s - &segs[0]];
-        for (uint32_t b = 0; b < (1u << (s->c - bsize_log2)); ++b) {
-          SegBlock B{};
-          B.first_slot = sl;
-          B.blk_in_seg = b;
-          B.log2cap = uint8_t(s->c);
-          B.nrounds = uint8_t(L0.P.nrounds);
-          B.final_pass = (L0.kind == PASS_MERGE && s->c == p) ? 1 : 0;
-          B.fill = 0;
-          blocks.push_back(B);
-        }
-      }
-      bl.nblocks = uint32_t(blocks.size()) - bl.first_block;
-      big.push_back(bl);
-    }
-  }
+  for (const BatchSeg& s : segs) cmax = std::max(cmax, s.c);
+  const Tuning tn = batch_tuning(kk, has_vals, cmax);
+  BatchTables bt;
+  int rc = batch_append(bt, kk, has_vals, tn, variant, segs, 0, 0);
+  for (int p = tn.t + 1; p <= cmax && rc == DARM_OK; ++p)
+    rc = batch_append(bt, kk, has_vals, tn, variant, segs, p, 0);
+  if (rc != DARM_OK) return rc;
 
   // singletons
   std::vector<uint64_t> sbase;
   std::vector<uint32_t> sld;
-  for (const SegInfo& s : segs)
+  for (const BatchSeg& s : segs)
     if (s.c == 0) {
       sbase.push_back(s.base);
       sld.push_back((s.len ? 1u : 0u) | (s.desc ? 2u : 0u));
     }
 
-  // --- upload ---------------------------------------------------------------
-  if (!slots.empty()) {
-    if (cudaMalloc(&sp.d_slots, slots.size() * sizeof(SegSlot)) != cudaSuccess) return DARM_ERR_OOM;
-    cudaMemcpy(sp.d_slots, slots.data(), slots.size() * sizeof(SegSlot), cudaMemcpyHostToDevice);
+  // upload
+  if (!bt.slots.empty()) {
+    if (cudaMalloc(&sp.d_slots, bt.slots.size() * sizeof(SegSlot)) != cudaSuccess) return DARM_ERR_OOM;
+    cudaMemcpy(sp.d_slots, bt.slots.data(), bt.slots.size() * sizeof(SegSlot), cudaMemcpyHostToDevice);
   }
-  if (!blocks.empty()) {
-    if (cudaMalloc(&sp.d_blocks, blocks.size() * sizeof(SegBlock)) != cudaSuccess) return DARM_ERR_OOM;
-    cudaMemcpy(sp.d_blocks, blocks.data(), blocks.size() * sizeof(SegBlock), cudaMemcpyHostToDevice);
+  if (!bt.blocks.empty()) {
+    if (cudaMalloc(&sp.d_blocks, bt.blocks.size() * sizeof(SegBlock)) != cudaSuccess) return DARM_ERR_OOM;
+    cudaMemcpy(sp.d_blocks, bt.blocks.data(), bt.blocks.size() * sizeof(SegBlock),
+               cudaMemcpyHostToDevice);
   }
-  if (cudaMalloc(&sp.d_counter, sizeof(unsigned int)) != cudaSuccess) return DARM_ERR_OOM;
+  const size_t ncounters = std::max<size_t>(1, bt.persistent.size());
+  if (cudaMalloc(&sp.d_counter, ncounters * sizeof(unsigned int)) != cudaSuccess) return DARM_ERR_OOM;
   if (!sbase.empty()) {
     sp.n_single = uint32_t(sbase.size());
     cudaMalloc(&sp.d_single_base, sbase.size() * sizeof(uint64_t));
@@ -288,73 +126,17 @@ int build_seg_plan(SegPlan& sp, uint32_t* keys, uint32_t* vals, const std::vecto
     cudaMemcpy(sp.d_single_ld, sld.data(), sld.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
   }
   if (cudaGetLastError() != cudaSuccess) return DARM_ERR_CUDA;
+  batch_bind(bt, sp.d_blocks, sp.d_slots, sp.d_counter);
+  sp.launches = bt.launches;
 
-  // --- launches -------------------------------------------------------------
-  sp.launches.clear();
-  if (tile_blocks > 0) {
-    Launch L{};
-    L.kind = PASS_TILE;
-    L.loge = e;
-    L.variant = (variant == DARM_AUTO) ? tn.var[PASS_TILE] : variant;
-    L.threads = 1u << (t - e);
-    L.smem = tile_smem;
-    L.P.b = L.P.c = L.P.w0 = uint32_t(t);
-    L.P.s = 0;
-    L.P.log2cap = uint32_t(t);
-    std::vector<Round> rs = tile_rounds(t, e);
-    L.P.nrounds = uint32_t(rs.size());
-    for (size_t r = 0; r < rs.size(); ++r) L.P.rounds[r] = rs[r];
-    L.P.blocks = sp.d_blocks;
-    L.P.slots = sp.d_slots;
-    L.fixed = fixed_kernel_fn(kk, has_vals, e, t, L.variant, false) != nullptr;
-    if (L.fixed) {
-      const void* fn = fixed_kernel_fn(kk, has_vals, e, t, L.variant, false);
-      L.P.work_counter = sp.d_counter;
-      L.P.nblocks = tile_blocks;
-      L.grid = uint32_t(std::min<int>(int(tile_blocks), occupancy_grid(fn, int(L.threads), L.smem)));
-    } else {
-      L.grid = tile_blocks;
-    }
-    sp.launches.push_back(L);
-  }
-  for (const TinyLaunch& tl : tiny) {
-    Launch L{};
-    L.kind = PASS_TILE;
-    L.fixed = false;
-    L.loge = tl.c;
-    L.variant = (variant == DARM_AUTO) ? tn.var[PASS_TILE] : variant;
-    L.threads = 1u << tiny_threads_log2;
-    L.grid = tl.nblocks;
-    L.smem = 0;
-    L.P.b = L.P.c = L.P.w0 = uint32_t(tl.c + tiny_threads_log2);
-    L.P.s = 0;
-    L.P.log2cap = uint32_t(tl.c);
-    std::vector<Round> rs = tile_rounds(tl.c, tl.c);
-    L.P.nrounds = 1;
-    L.P.rounds[0] = rs[0];
-    L.P.blocks = sp.d_blocks + tl.first_block;
-    L.P.slots = sp.d_slots;
-    sp.launches.push_back(L);
-  }
-  for (const BigLaunch& bl : big) {
-    Launch L = bl.L;
-    L.grid = bl.nblocks;
-    L.P.blocks = sp.d_blocks + bl.first_block;
-    L.P.slots = sp.d_slots;
-    L.P.log2cap = 0;
-    L.P.map_in = L.P.map_out = 0;
-    sp.launches.push_back(L);
-  }
-
-  // --- capture --------------------------------------------------------------
+  // capture
   cudaStream_t cs;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return DARM_ERR_CUDA;
-  int rc = DARM_OK;
   if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaStreamDestroy(cs);
     return DARM_ERR_CUDA;
   }
-  cudaMemsetAsync(sp.d_counter, 0, sizeof(unsigned int), cs);
+  cudaMemsetAsync(sp.d_counter, 0, ncounters * sizeof(unsigned int), cs);
   rc = launch_plan(sp.launches, kk, keys, vals, cs, /*count=*/false);
   if (rc == DARM_OK && sp.n_single) {
     seg_singletons_kernel<<<(sp.n_single + 255) / 256, 256, 0, cs>>>(keys, vals, sp.d_single_base,
@@ -406,7 +188,7 @@ extern "C" int darm_segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_
   if ((reinterpret_cast<uintptr_t>(keys) & 15u) != 0) return DARM_ERR_INVALID_ARG;
   if (vals && (reinterpret_cast<uintptr_t>(vals) & 15u) != 0) return DARM_ERR_INVALID_ARG;
 
-  std::vector<SegInfo> segs;
+  std::vector<BatchSeg> segs;
   segs.reserve(num_segs);
   for (uint32_t s = 0; s < num_segs; ++s) {
     const uint64_t a = seg_offsets[s], b = seg_offsets[s + 1];
@@ -417,8 +199,7 @@ extern "C" int darm_segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_
     if (cap > (uint64_t(1) << 31)) return DARM_ERR_INVALID_ARG;
     if ((a & (std::min<uint64_t>(cap, 4) - 1)) != 0) return DARM_ERR_INVALID_ARG;
     if (seg_len[s] > cap) return DARM_ERR_INVALID_ARG;
-    SegInfo si;
-    si.idx = s;
+    BatchSeg si;
     si.base = a;
     si.len = seg_len[s];
     si.c = log2u(cap);
