@@ -37,7 +37,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["darm", "reference"], default="darm")
-    ap.add_argument("--workload", choices=["kv24", "kv24skew", "f32"], default="kv24")
+    ap.add_argument("--workload", choices=["kv24", "kv24skew", "f32", "seg", "serve"],
+                    default="kv24")
+    ap.add_argument("--serve-requests", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -199,11 +201,150 @@ def cpu_baseline(keys, vals):
                       f"({dt:.1f} s)"}
 
 
+def run_segmented(args, world, rank, local):
+    """Batched segmented sort: 10,000 uint32 arrays, log-uniform real lengths
+    32..65536 padded to powers of two, one graph replay per step."""
+    import numpy as np
+    import torch
+
+    import paper_2107_05681_gb300 as darm
+    import synth
+    segs = synth.cfg4_segments()
+    real = int(segs.lengths.astype(np.int64).sum())
+    padded = int(segs.offsets[-1])
+    src_k = torch.from_numpy(segs.keys).cuda()
+    src_v = torch.from_numpy(segs.vals).cuda()
+    k, v = torch.empty_like(src_k), torch.empty_like(src_v)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {}
+    launches = 0
+    for variant in ("melded", "divergent"):
+        for _ in range(args.warmup):
+            k.copy_(src_k)
+            v.copy_(src_v)
+            darm.segmented_sort(k, v, segs.offsets, segs.lengths, variant=variant)
+        torch.cuda.synchronize()
+        barrier(world)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        l0 = darm.launch_count()
+        for a, b in evs:
+            k.copy_(src_k)
+            v.copy_(src_v)
+            flush.fill_(1.0)
+            a.record(stream)
+            darm.segmented_sort(k, v, segs.offsets, segs.lengths, variant=variant)
+            b.record(stream)
+        torch.cuda.synchronize()
+        launches += darm.launch_count() - l0
+        ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), world)
+        out[variant] = ms
+    if rank == 0:
+        ms = out["melded"]
+        line = {
+            "metric": "batched segmented sort: real keys/s (melded vs divergent)",
+            "value": world * real * args.steps / (ms * 1e-3), "unit": "keys/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "10,000 uint32 key-value segments, real lengths log-uniform "
+                                   "32..65536, sentinel-padded to powers of two",
+                       "real_keys": real, "padded_keys": padded,
+                       "l2": "flushed between steps"},
+            "padded_keys_per_s": world * padded * args.steps / (ms * 1e-3),
+            "divergent": {"value": world * real * args.steps / (out["divergent"] * 1e-3),
+                          "ms_per_step": out["divergent"] / args.steps},
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def run_serving(args, world, rank, local):
+    """Poisson arrivals of uint64 key-value sort requests, sizes 2^U(8,20),
+    mixed directions, 4 GB budget: saturated throughput, then p50/p99 latency
+    at 50/80/95 % of it, for both kernel forms."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_2107_05681_gb300 as darm
+    import synth
+    count = args.serve_requests
+    reqs = synth.cfg5_requests(count=count, materialize=False)
+    bank = torch.from_numpy(synth.uniform_u64(synth.SEED_CFG5, 1 << 21)).cuda()
+    idx = torch.from_numpy(np.arange(1 << 20, dtype=np.uint32)).cuda()
+    offs = synth.below(synth.substream(synth.SEED_CFG5, 9), count, 1 << 20)
+
+    def make(r, i):
+        k = bank[int(offs[i]):int(offs[i]) + r.n].clone()
+        v = idx[:r.n].clone()
+        return k, v
+
+    def run(variant, rate):
+        darm.serve_start(budget_bytes=4 << 30, max_inflight=256, variant=variant,
+                         num_streams=2)
+        bufs = [make(r, i) for i, r in enumerate(reqs)]
+        torch.cuda.synchronize()
+        ids = [None] * count
+        t0 = time.perf_counter()
+        if rate is None:
+            for i, ((k, v), r) in enumerate(zip(bufs, reqs)):
+                ids[i] = darm.serve_submit(k, v, descending=r.desc)
+        else:
+            gaps = -np.log(synth.uniform01(synth.substream(synth.SEED_CFG5, 11), count)) / rate
+            t = 0.0
+            for i, ((k, v), r) in enumerate(zip(bufs, reqs)):
+                t += gaps[i]
+                dt = t0 + t - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                ids[i] = darm.serve_submit(k, v, descending=r.desc)
+        for rid in ids:
+            darm.serve_wait(rid, 600000)
+        wall = time.perf_counter() - t0
+        p50, p99, kps, done = darm.serve_stats()
+        darm.serve_stop()
+        keys = sum(r.n for r in reqs)
+        return {"p50_ms": p50, "p99_ms": p99, "keys_per_s": keys / wall,
+                "offered_req_per_s": rate, "completed": done}
+
+    res = {}
+    for variant in ("melded", "divergent"):
+        sat = run(variant, None)
+        req_rate = count / (sum(r.n for r in reqs) / sat["keys_per_s"])
+        loads = {}
+        for frac in (0.5, 0.8, 0.95):
+            loads[str(frac)] = run(variant, frac * req_rate)
+        res[variant] = {"saturated": sat, "loads": loads}
+    if rank == 0:
+        line = {
+            "metric": "serving: keys/s and p50/p99 latency, melded vs divergent",
+            "value": res["melded"]["saturated"]["keys_per_s"], "unit": "keys/s",
+            "n_gpus": world, "steps": count, "warmup": 0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"{count} uint64 key-value sort requests, sizes 2^U(8,20), "
+                                   "direction Bernoulli(0.5), 4 GB budget, Poisson arrivals",
+                       "max_inflight": 256, "streams": 2},
+            "melded": res["melded"], "divergent": res["divergent"],
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload in ("seg", "serve"):
+        import torch
+
+        import paper_2107_05681_gb300 as darm
+        torch.cuda.set_device(local)
+        darm.init(local)
+        (run_segmented if args.workload == "seg" else run_serving)(args, world, rank, local)
         return
     import numpy as np
     import torch
@@ -261,7 +402,7 @@ def main():
     got = work_k.cpu().numpy()
     if keys_np.dtype == np.float32:
         gw = got.view(np.uint32)
-        mapped = np.where(gw >> 31, gw ^ np.uint32(0x80000000), ~gw)
+        mapped = np.where((gw >> np.uint32(31)) != 0, ~gw, gw | np.uint32(0x80000000))
         assert np.all(mapped[1:] >= mapped[:-1]), "result not sorted"
     else:
         assert np.all(got[1:] >= got[:-1]), "result not sorted"

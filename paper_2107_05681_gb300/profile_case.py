@@ -1,0 +1,37 @@
+"""Run one workload's sort twice (a warm-up and the captured one) so that a
+profiler can capture the second sort's kernel launches.
+
+    python -m paper_2107_05681_gb300.profile_case VARIANT WORKLOAD
+
+VARIANT: melded | divergent.  WORKLOAD: cfg1 (4096 uint32 keys, one block),
+kv24 (2^24 uint32 key-value pairs), f32 (2^26 float32 keys).
+"""
+import sys
+
+import numpy as np
+import torch
+
+import paper_2107_05681_gb300 as darm
+import synth
+
+
+def main(variant="melded", workload="kv24"):
+    darm.init(0)
+    if workload == "kv24":
+        k, v = synth.cfg2_kv()
+    elif workload == "cfg1":
+        k, v = synth.cfg1_keys(), None
+    else:
+        k, v = synth.cfg3_f32(), None
+    K = torch.from_numpy(k).cuda()
+    V = torch.from_numpy(v).cuda() if v is not None else None
+    for _ in range(2):
+        K2 = K.clone()
+        V2 = V.clone() if V is not None else None
+        darm.sort(K2, V2, variant=variant)
+    torch.cuda.synchronize()
+    print("ok", darm.launch_count())
+
+
+if __name__ == "__main__":
+    main(*sys.argv[1:3])
