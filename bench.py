@@ -181,6 +181,31 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def kernel_sources_sha256():
+    """Hash of the CUDA sources; a recorded DRAM traffic figure is used only
+    while the kernels are unchanged since it was captured."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2107_05681_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(os.path.basename(f).encode())
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(workload_name, pass_kind):
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_sources_sha256") != kernel_sources_sha256():
+        return None
+    return rec.get(workload_name, {}).get(pass_kind)
+
+
 def cpu_baseline(keys, vals):
     """Oracle keys/s on a bounded sample (about 10-20 s of one core)."""
     import numpy as np
@@ -476,7 +501,9 @@ def main():
             "divergent": {"value": value_div, "ms_per_step": ms_div / args.steps},
             "melded_over_divergent": value / value_div,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": f"{dom} pass",
+                         "frac": achieved / peak,
+                         "traffic": recorded_traffic(args.workload, dom),
+                         "algorithmic_bytes": bytes_per_launch, "kernel": f"{dom} pass",
                          "peak_source": peak_src,
                          "whole_sort_gbs": whole_sort_gbs,
                          "whole_sort_frac": whole_sort_gbs / peak,
