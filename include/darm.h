@@ -135,6 +135,30 @@ int darm_segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* seg_offs
                         const uint32_t* seg_len, uint32_t num_segs, int dir,
                         int variant, const uint8_t* seg_desc, void* stream);
 
+/* Same sort as darm_segmented_sort for callers that cannot allocate device
+ * memory - e.g. an application whose own allocator owns the whole GPU, or a
+ * latency-critical loop that cannot take the device synchronisation
+ * cudaMalloc/cudaFree bring.  (The paper has no counterpart; this is a
+ * service of this library.)  The block tables and work counter that
+ * darm_segmented_sort keeps in buffers it allocates are instead copied, on
+ * `stream`, into one 1 MiB array compiled into the library, right before each
+ * launch; nothing is allocated on the device and no graph is built.
+ *   - Limit: the tables of any single launch must fit in 1 MiB (16 bytes per
+ *     segment of a phase plus 16 bytes per block; roughly up to 30,000
+ *     segments or 60,000 blocks of a tile); larger layouts are rejected with
+ *     DARM_ERR_INVALID_ARG and a message on stderr, before anything is
+ *     enqueued.
+ *   - The array is shared by every call and keeps the last call's contents:
+ *     calls whose work overlaps on the GPU (other streams, other host
+ *     threads) race on it.  Calls on one stream are ordered and safe.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture.
+ * Arguments, layout rules and results are those of darm_segmented_sort. */
+int darm_segmented_sort_noalloc(uint32_t* keys, uint32_t* vals, const uint64_t* seg_offsets,
+                                const uint32_t* seg_len, uint32_t num_segs, int dir,
+                                int variant, const uint8_t* seg_desc, void* stream);
+
 /* ---- tuning ----------------------------------------------------------- */
 
 /* Time candidate tile sizes, elements per thread and per-stage variants for

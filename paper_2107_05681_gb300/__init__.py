@@ -57,6 +57,8 @@ _sig = {
     "darm_bitonic_sort_u64": ([_vp, _vp, _sz, _i32, _i32, _vp], _i32),
     "darm_bitonic_sort_host": ([_vp, _vp, _sz, _i32, _i32, _i32], _i32),
     "darm_segmented_sort": ([_vp, _vp, _vp, _vp, ctypes.c_uint32, _i32, _i32, _vp, _vp], _i32),
+    "darm_segmented_sort_noalloc": ([_vp, _vp, _vp, _vp, ctypes.c_uint32, _i32, _i32, _vp, _vp],
+                                    _i32),
     "darm_autotune": ([_i32, _sz, _i32, ctypes.c_char_p], _i32),
     "darm_load_tune_db": ([ctypes.c_char_p], _i32),
     "darm_plan_info": ([_i32, _sz, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
@@ -200,6 +202,32 @@ def segmented_sort(keys, vals, offsets, lengths, descending: bool = False, varia
                                  DESC if descending else ASC, _variant(variant), dp,
                                  _stream_handle(stream))
     _check(rc, "darm_segmented_sort")
+
+
+def segmented_sort_noalloc(keys, vals, offsets, lengths, descending: bool = False,
+                           variant="melded", seg_desc=None, stream=None) -> None:
+    """segmented_sort for callers that cannot let the library allocate device
+    memory: the per-launch tables go through a fixed 1 MiB array inside the
+    library (shared by all calls; calls overlapping on the GPU race)."""
+    import numpy as np
+    import torch
+    if keys.dtype != torch.uint32 or not keys.is_cuda or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous uint32 CUDA tensor")
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    ln = np.ascontiguousarray(lengths, dtype=np.uint32)
+    if off.size != ln.size + 1:
+        raise ValueError("offsets must have num_segments + 1 entries")
+    dp = None
+    if seg_desc is not None:
+        dd = np.ascontiguousarray(seg_desc, dtype=np.uint8)
+        dp = dd.ctypes.data_as(ctypes.c_void_p)
+    vp = None if vals is None else ctypes.c_void_p(vals.data_ptr())
+    rc = lib.darm_segmented_sort_noalloc(ctypes.c_void_p(keys.data_ptr()), vp,
+                                         off.ctypes.data_as(ctypes.c_void_p),
+                                         ln.ctypes.data_as(ctypes.c_void_p), ln.size,
+                                         DESC if descending else ASC, _variant(variant), dp,
+                                         _stream_handle(stream))
+    _check(rc, "darm_segmented_sort_noalloc")
 
 
 def plan_info(dtype: int, n: int, has_vals: bool, variant="melded"):

@@ -10,6 +10,7 @@
 #include <tuple>
 #include <vector>
 
+#include "batch.h"
 #include "plan.h"
 
 namespace darm {
@@ -48,5 +49,14 @@ const std::vector<Launch>* cached_plan(KeyKind kk, bool has_vals, int m, int var
 int sort_device(KeyKind kk, bool f32, void* keys, uint32_t* vals, size_t n, int dir, int variant,
                 cudaStream_t stream);
 void segmented_release_all();
+
+// Validate a segment layout (host arrays) and list its non-empty segments.
+int segmented_parse(const uint64_t* seg_offsets, const uint32_t* seg_len, uint32_t num_segs, int dir,
+                    const uint8_t* seg_desc, std::vector<BatchSeg>& segs);
+
+// Capacity-1 segments: write the sentinel into the empty ones.  base[i] is
+// the element offset, len_desc[i] bit 0 = real length 1, bit 1 = descending.
+void launch_singletons(uint32_t* keys, uint32_t* vals, const uint64_t* base,
+                       const uint32_t* len_desc, uint32_t n, cudaStream_t s);
 
 }  // namespace darm

@@ -51,6 +51,16 @@ __global__ void seg_singletons_kernel(uint32_t* keys, uint32_t* vals, const uint
   }
 }
 
+}  // namespace
+
+void launch_singletons(uint32_t* keys, uint32_t* vals, const uint64_t* base,
+                       const uint32_t* len_desc, uint32_t n, cudaStream_t s) {
+  if (n == 0) return;
+  seg_singletons_kernel<<<(n + 255) / 256, 256, 0, s>>>(keys, vals, base, len_desc, n);
+}
+
+namespace {
+
 struct SegPlan {
   std::vector<Launch> launches;
   SegSlot* d_slots = nullptr;
@@ -139,8 +149,7 @@ int build_seg_plan(SegPlan& sp, uint32_t* keys, uint32_t* vals, const std::vecto
   cudaMemsetAsync(sp.d_counter, 0, ncounters * sizeof(unsigned int), cs);
   rc = launch_plan(sp.launches, kk, keys, vals, cs, /*count=*/false);
   if (rc == DARM_OK && sp.n_single) {
-    seg_singletons_kernel<<<(sp.n_single + 255) / 256, 256, 0, cs>>>(keys, vals, sp.d_single_base,
-                                                                       sp.d_single_ld, sp.n_single);
+    launch_singletons(keys, vals, sp.d_single_base, sp.d_single_ld, sp.n_single, cs);
   }
   cudaGraph_t graph = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
@@ -167,6 +176,29 @@ uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
 
 }  // namespace
 
+int segmented_parse(const uint64_t* seg_offsets, const uint32_t* seg_len, uint32_t num_segs, int dir,
+                    const uint8_t* seg_desc, std::vector<BatchSeg>& segs) {
+  segs.clear();
+  segs.reserve(num_segs);
+  for (uint32_t s = 0; s < num_segs; ++s) {
+    const uint64_t a = seg_offsets[s], b = seg_offsets[s + 1];
+    if (b < a) return DARM_ERR_INVALID_ARG;
+    const uint64_t cap = b - a;
+    if (cap == 0) continue;
+    if ((cap & (cap - 1)) != 0) return DARM_ERR_NOT_POW2;
+    if (cap > (uint64_t(1) << 31)) return DARM_ERR_INVALID_ARG;
+    if ((a & (std::min<uint64_t>(cap, 4) - 1)) != 0) return DARM_ERR_INVALID_ARG;
+    if (seg_len[s] > cap) return DARM_ERR_INVALID_ARG;
+    BatchSeg si;
+    si.base = a;
+    si.len = seg_len[s];
+    si.c = log2u(cap);
+    si.desc = seg_desc ? (seg_desc[s] != 0) : (dir == DARM_DESC);
+    segs.push_back(si);
+  }
+  return DARM_OK;
+}
+
 void segmented_release_all() {
   std::lock_guard<std::mutex> lk(g_seg_mu);
   if (!g_seg_plans.empty()) cudaDeviceSynchronize();
@@ -189,23 +221,8 @@ extern "C" int darm_segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_
   if (vals && (reinterpret_cast<uintptr_t>(vals) & 15u) != 0) return DARM_ERR_INVALID_ARG;
 
   std::vector<BatchSeg> segs;
-  segs.reserve(num_segs);
-  for (uint32_t s = 0; s < num_segs; ++s) {
-    const uint64_t a = seg_offsets[s], b = seg_offsets[s + 1];
-    if (b < a) return DARM_ERR_INVALID_ARG;
-    const uint64_t cap = b - a;
-    if (cap == 0) continue;
-    if ((cap & (cap - 1)) != 0) return DARM_ERR_NOT_POW2;
-    if (cap > (uint64_t(1) << 31)) return DARM_ERR_INVALID_ARG;
-    if ((a & (std::min<uint64_t>(cap, 4) - 1)) != 0) return DARM_ERR_INVALID_ARG;
-    if (seg_len[s] > cap) return DARM_ERR_INVALID_ARG;
-    BatchSeg si;
-    si.base = a;
-    si.len = seg_len[s];
-    si.c = log2u(cap);
-    si.desc = seg_desc ? (seg_desc[s] != 0) : (dir == DARM_DESC);
-    segs.push_back(si);
-  }
+  const int prc = segmented_parse(seg_offsets, seg_len, num_segs, dir, seg_desc, segs);
+  if (prc != DARM_OK) return prc;
   if (segs.empty()) return DARM_OK;
 
   // layout key: pointers, direction, variant and a hash of the arrays
