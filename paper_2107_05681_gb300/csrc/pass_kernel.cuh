@@ -189,6 +189,12 @@ __device__ __forceinline__ void ce_side(K& a, K& b, uint32_t& va, uint32_t& vb) 
 //     2^(a-3)), a multiply-add instead of bit twiddling.
 __device__ __forceinline__ uint32_t phys(uint32_t l) { return l + ((l >> 5) << 2); }
 
+// Key-value passes with 32-bit keys keep (key, payload) pairs together in
+// 8-byte slots: pair l at slot phys8(l) = l + 2 * (l / 16).  The slot count
+// of a tile equals the word count of phys(), so both layouts share
+// smem_words().
+__device__ __forceinline__ uint32_t phys8(uint32_t l) { return l + ((l >> 4) << 1); }
+
 __host__ __device__ constexpr uint32_t smem_words(uint32_t elems) {
   return elems + ((elems >> 5) << 2) + 4;
 }
@@ -269,6 +275,36 @@ __device__ __forceinline__ void load_elems(K (&kr)[1 << LOGE], uint32_t (&vr)[1 
           const int r = REV ? (E - 1 - r0) : r0;
           vr[r] = gv[A.g_t + (uint32_t(r) << A.gsh)];
         }
+      }
+    }
+  } else if (V && sizeof(K) == 4) {
+    // interleaved (key, payload) slots
+    const uint2* s2 = reinterpret_cast<const uint2*>(sk);
+    if (A.a == 0 && E >= 2) {
+#pragma unroll
+      for (int q0 = 0; q0 < E / 2; ++q0) {
+        const int q = REV ? (E / 2 - 1 - q0) : q0;
+        const uint4 w = *reinterpret_cast<const uint4*>(s2 + A.s_base + phys8(uint32_t(2 * q)));
+        kr[2 * q] = kx(K(w.x), m);
+        vr[2 * q] = w.y;
+        kr[2 * q + 1] = kx(K(w.z), m);
+        vr[2 * q + 1] = w.w;
+      }
+    } else if (A.a >= 5) {
+#pragma unroll
+      for (int r0 = 0; r0 < E; ++r0) {
+        const int r = REV ? (E - 1 - r0) : r0;
+        const uint2 w = s2[A.s_base + uint32_t(r) * A.stride];
+        kr[r] = kx(K(w.x), m);
+        vr[r] = w.y;
+      }
+    } else {
+#pragma unroll
+      for (int r0 = 0; r0 < E; ++r0) {
+        const int r = REV ? (E - 1 - r0) : r0;
+        const uint2 w = s2[A.s_base + phys8(uint32_t(r) << A.a)];
+        kr[r] = kx(K(w.x), m);
+        vr[r] = w.y;
       }
     }
   } else {
@@ -366,6 +402,32 @@ __device__ __forceinline__ void store_elems(const K (&kr)[1 << LOGE], const uint
           const int r = REV ? (E - 1 - r0) : r0;
           gv[A.g_t + (uint32_t(r) << A.gsh)] = vr[r];
         }
+      }
+    }
+  } else if (V && sizeof(K) == 4) {
+    uint2* s2 = reinterpret_cast<uint2*>(sk);
+    if (A.a == 0 && E >= 2) {
+#pragma unroll
+      for (int q0 = 0; q0 < E / 2; ++q0) {
+        const int q = REV ? (E / 2 - 1 - q0) : q0;
+        uint4 w;
+        w.x = uint32_t(kx(kr[2 * q], m));
+        w.y = vr[2 * q];
+        w.z = uint32_t(kx(kr[2 * q + 1], m));
+        w.w = vr[2 * q + 1];
+        *reinterpret_cast<uint4*>(s2 + A.s_base + phys8(uint32_t(2 * q))) = w;
+      }
+    } else if (A.a >= 5) {
+#pragma unroll
+      for (int r0 = 0; r0 < E; ++r0) {
+        const int r = REV ? (E - 1 - r0) : r0;
+        s2[A.s_base + uint32_t(r) * A.stride] = make_uint2(uint32_t(kx(kr[r], m)), vr[r]);
+      }
+    } else {
+#pragma unroll
+      for (int r0 = 0; r0 < E; ++r0) {
+        const int r = REV ? (E - 1 - r0) : r0;
+        s2[A.s_base + phys8(uint32_t(r) << A.a)] = make_uint2(uint32_t(kx(kr[r], m)), vr[r]);
       }
     }
   } else {
@@ -523,7 +585,7 @@ __global__ void __launch_bounds__(MAXT, 1) darm_pass_kernel(const __grid_constan
     RoundAddr A;
     A.a = a;
     A.gsh = (a >= P.c) ? (a - P.c + P.w0) : a;
-    A.s_base = phys(tl);
+    A.s_base = (V && sizeof(K) == 4) ? phys8(tl) : phys(tl);
     A.stride = (a >= 5) ? ((1u << a) + (1u << (a - 3))) : 0u;
     const bool vec = (a == 0) && (P.c >= uint32_t(LOGE));
     uint32_t min_ = 0, mout = 0;

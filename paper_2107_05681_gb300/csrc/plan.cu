@@ -42,7 +42,7 @@ Tuning default_tuning(KeyKind kk, bool has_vals) {
   Tuning tn;
   if (words == 1) {
     tn.t = 14;  // 16 Ki uint32 keys = 64 KiB of shared memory per tile
-    tn.e1 = 4;
+    tn.e1 = 5;  // 32 keys per thread: five layers per shared-memory round
     tn.e2 = 4;
     tn.c2 = 8;
     tn.w2 = 2;

@@ -109,6 +109,19 @@ __device__ __forceinline__ void static_for(F&& f) {
   }
 }
 
+// Key-value tiles with 32-bit keys keep each (key, payload) pair together in
+// one 8-byte shared-memory slot, so one 64-bit access moves both.  Pair l
+// lives at slot phys8(l) = l + 2 * (l / 16): two pad slots after every 16
+// pairs keep the bottom window's 16-byte accesses and the lanes of the
+// higher windows on distinct banks.  phys8 is additive over disjoint bits,
+// like phys.
+template <typename K, bool V>
+struct Interleave {
+  static constexpr bool value = V && sizeof(K) == 4;
+};
+__host__ __device__ constexpr uint32_t phys8_c(uint32_t l) { return l + ((l >> 4) << 1); }
+__host__ __device__ constexpr uint32_t phys_c(uint32_t l) { return l + ((l >> 5) << 2); }
+
 // Static-offset element access: register r of a round with window A sits at
 // local index tl | (r << A); phys() is additive over disjoint bits, so its
 // shared-memory word is phys(tl) + phys(r << A), a compile-time offset.
@@ -149,6 +162,27 @@ __device__ __forceinline__ void s_load(K (&kr)[1 << LOGE], uint32_t (&vr)[1 << L
         const int r = REV ? (E - 1 - r0) : r0;
         kr[r] = key_in<K>(gk[g_t + (uint32_t(r) << A)], mapf) ^ m;
         if (V) vr[r] = gv[g_t + (uint32_t(r) << A)];
+      }
+    }
+  } else if constexpr (Interleave<K, V>::value) {
+    const uint2* s2 = reinterpret_cast<const uint2*>(sk);
+    if constexpr (A == 0) {
+#pragma unroll
+      for (int q0 = 0; q0 < E / 2; ++q0) {
+        const int q = REV ? (E / 2 - 1 - q0) : q0;
+        const uint4 w = *reinterpret_cast<const uint4*>(s2 + s_base + phys8_c(uint32_t(2 * q)));
+        kr[2 * q] = K(w.x) ^ m;
+        vr[2 * q] = w.y;
+        kr[2 * q + 1] = K(w.z) ^ m;
+        vr[2 * q + 1] = w.w;
+      }
+    } else {
+#pragma unroll
+      for (int r0 = 0; r0 < E; ++r0) {
+        const int r = REV ? (E - 1 - r0) : r0;
+        const uint2 w = s2[s_base + phys8_c(uint32_t(r) << A)];
+        kr[r] = K(w.x) ^ m;
+        vr[r] = w.y;
       }
     }
   } else {
@@ -226,6 +260,26 @@ __device__ __forceinline__ void s_store(const K (&kr)[1 << LOGE], const uint32_t
         const int r = REV ? (E - 1 - r0) : r0;
         gk[g_t + (uint32_t(r) << A)] = key_out<K>(kr[r] ^ m, mapf);
         if (V) gv[g_t + (uint32_t(r) << A)] = vr[r];
+      }
+    }
+  } else if constexpr (Interleave<K, V>::value) {
+    uint2* s2 = reinterpret_cast<uint2*>(sk);
+    if constexpr (A == 0) {
+#pragma unroll
+      for (int q0 = 0; q0 < E / 2; ++q0) {
+        const int q = REV ? (E / 2 - 1 - q0) : q0;
+        uint4 w;
+        w.x = uint32_t(kr[2 * q] ^ m);
+        w.y = vr[2 * q];
+        w.z = uint32_t(kr[2 * q + 1] ^ m);
+        w.w = vr[2 * q + 1];
+        *reinterpret_cast<uint4*>(s2 + s_base + phys8_c(uint32_t(2 * q))) = w;
+      }
+    } else {
+#pragma unroll
+      for (int r0 = 0; r0 < E; ++r0) {
+        const int r = REV ? (E - 1 - r0) : r0;
+        s2[s_base + phys8_c(uint32_t(r) << A)] = make_uint2(uint32_t(kr[r] ^ m), vr[r]);
       }
     }
   } else {
@@ -313,7 +367,7 @@ __device__ __forceinline__ void tile_block(const PassParams& P, uint32_t bidx, K
     const bool to_global = last || (R.dst == LOC_GLOBAL);
     const uint32_t tl = (tid & ((1u << A) - 1u)) | ((tid >> A) << (A + LOGE));
     const uint32_t g_full = tl | gblk;
-    const uint32_t s_base = phys(tl);
+    const uint32_t s_base = Interleave<K, V>::value ? phys8(tl) : phys(tl);
     uint32_t min_ = 0, mout = 0, g_t = g_full;
     K* bk = gk;
     uint32_t* bv = gv;

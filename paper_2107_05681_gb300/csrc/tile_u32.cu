@@ -23,7 +23,8 @@ struct Combo {
   bool v;
   int loge, logt;
 };
-constexpr Combo kCombos[] = {{false, 4, 12}, {false, 4, 13}, {false, 4, 14}, {true, 4, 12}, {true, 4, 13}};
+constexpr Combo kCombos[] = {{false, 4, 12}, {false, 4, 13}, {false, 4, 14}, {true, 4, 12},
+                             {true, 4, 13}, {true, 5, 13}, {false, 5, 14}};
 
 }  // namespace
 
@@ -33,6 +34,8 @@ KernelEntry tile_kernel_u32(bool has_vals, int loge, int logt, int var, bool mer
   if (!has_vals && loge == 4 && logt == 14) return tpick<false, 4, 14>(var, merge);
   if (has_vals && loge == 4 && logt == 12) return tpick<true, 4, 12>(var, merge);
   if (has_vals && loge == 4 && logt == 13) return tpick<true, 4, 13>(var, merge);
+  if (has_vals && loge == 5 && logt == 13) return tpick<true, 5, 13>(var, merge);
+  if (!has_vals && loge == 5 && logt == 14) return tpick<false, 5, 14>(var, merge);
   return KernelEntry{nullptr, 0};
 }
 
@@ -61,6 +64,12 @@ int fixed_schedule_rounds(int logt, int loge, bool merge, SRound* out, int cap) 
   if (loge == 4 && logt == 14)
     return merge ? copy(Schedule<14, 4, true>::value, Schedule<14, 4, true>::count)
                  : copy(Schedule<14, 4, false>::value, Schedule<14, 4, false>::count);
+  if (loge == 5 && logt == 13)
+    return merge ? copy(Schedule<13, 5, true>::value, Schedule<13, 5, true>::count)
+                 : copy(Schedule<13, 5, false>::value, Schedule<13, 5, false>::count);
+  if (loge == 5 && logt == 14)
+    return merge ? copy(Schedule<14, 5, true>::value, Schedule<14, 5, true>::count)
+                 : copy(Schedule<14, 5, false>::value, Schedule<14, 5, false>::count);
   if (loge == 3 && logt == 12)
     return merge ? copy(Schedule<12, 3, true>::value, Schedule<12, 3, true>::count)
                  : copy(Schedule<12, 3, false>::value, Schedule<12, 3, false>::count);
