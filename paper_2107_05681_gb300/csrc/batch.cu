@@ -35,6 +35,7 @@ constexpr int kTinyThreadsLog2 = 7;
 
 Tuning batch_tuning(KeyKind kk, bool has_vals, int cmax) {
   Tuning tn = tuning_for(kk, has_vals, 0);
+  tn.tma = 0;  // batch passes resolve every block through a table
   fit_tuning(tn, kk, has_vals, std::max(cmax, tn.t), g_ctx.smem_limit);
   return tn;
 }

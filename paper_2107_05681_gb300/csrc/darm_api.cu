@@ -40,9 +40,10 @@ int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_
     P.keys = keys;
     P.vals = vals;
     P.status = g_ctx.d_status;
-    const void* fn = L.fixed ? fixed_kernel_fn(kk, has_vals, L.loge, int(L.P.b), L.variant,
-                                               L.kind == PASS_MERGE)
-                             : kernel_fn(kk, has_vals, L.loge, L.variant);
+    const void* fn =
+        L.tma ? tma_merge_kernel_u32(has_vals, L.loge, int(L.P.b), L.variant, nullptr).fn
+        : L.fixed ? fixed_kernel_fn(kk, has_vals, L.loge, int(L.P.b), L.variant, L.kind == PASS_MERGE)
+                  : kernel_fn(kk, has_vals, L.loge, L.variant);
     if (!fn) return DARM_ERR_INVALID_ARG;
     void* args[] = {&P};
     cudaError_t err = cudaLaunchKernel(fn, dim3(L.grid), dim3(L.threads), args, L.smem, stream);
@@ -72,7 +73,7 @@ const std::vector<Launch>* cached_plan(KeyKind kk, bool has_vals, int m, int var
                                        uint32_t map_in, uint32_t map_out) {
   const Tuning tn = tuning_for(kk, has_vals, m);
   PlanKey key{int(kk), int(has_vals), m, variant, map_in, map_out, tn.t, tn.e1, tn.e2, tn.c2,
-              tn.w2, tn.var[0] * 4 + tn.var[1] * 2 + tn.var[2]};
+              tn.w2 * 16 + tn.tma, tn.var[0] * 4 + tn.var[1] * 2 + tn.var[2]};
   std::lock_guard<std::mutex> lk(g_ctx.mu);
   auto it = g_ctx.plans.find(key);
   if (it != g_ctx.plans.end()) return &it->second;
@@ -138,12 +139,14 @@ int darm_sort_init(int device, size_t workspace_bytes) {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   g_ctx.device = device;
   g_ctx.sms = sms;
+  g_sms_for_plans = sms;
   g_ctx.smem_limit = size_t(optin);
   int st[2] = {optin, 0};
   for_each_kernel_u32(set_smem_attr, st);
   for_each_kernel_u64(set_smem_attr, st);
   for_each_tile_kernel_u32(set_smem_attr, st);
   for_each_tile_kernel_u64(set_smem_attr, st);
+  for_each_tma_kernel_u32(set_smem_attr, st);
   if (st[1] != 0) {
     fprintf(stderr, "darm: configuring shared memory failed: %s\n",
             cudaGetErrorString(cudaError_t(st[1])));

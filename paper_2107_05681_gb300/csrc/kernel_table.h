@@ -21,11 +21,16 @@ KernelEntry kernel_u64(bool has_vals, int loge, int var);
 KernelEntry tile_kernel_u32(bool has_vals, int loge, int logt, int var, bool merge);
 KernelEntry tile_kernel_u64(bool has_vals, int loge, int logt, int var, bool merge);
 
+// Persistent merge kernels that prefetch tiles with bulk copies
+// (tma_merge.cuh); smem_bytes receives the dynamic shared memory they need.
+KernelEntry tma_merge_kernel_u32(bool has_vals, int loge, int logt, int var, size_t* smem_bytes);
+
 // Call fn(kernel address, ctx) for every instantiation (used to configure
 // shared-memory limits once per device).
 void for_each_kernel_u32(void (*fn)(const void*, void*), void* ctx);
 void for_each_kernel_u64(void (*fn)(const void*, void*), void* ctx);
 void for_each_tile_kernel_u32(void (*fn)(const void*, void*), void* ctx);
 void for_each_tile_kernel_u64(void (*fn)(const void*, void*), void* ctx);
+void for_each_tma_kernel_u32(void (*fn)(const void*, void*), void* ctx);
 
 }  // namespace darm

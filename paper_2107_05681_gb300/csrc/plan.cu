@@ -32,6 +32,8 @@ static bool has_fixed(KeyKind kk, bool has_vals, int loge, int logt) {
   return true;
 }
 
+int g_sms_for_plans = 152;
+
 static int max_threads(KeyKind kk, bool has_vals, int loge) {
   KernelEntry e = (kk == KEY_U32) ? kernel_u32(has_vals, loge, 1) : kernel_u64(has_vals, loge, 1);
   return e.fn ? e.max_threads : 0;
@@ -43,21 +45,24 @@ Tuning default_tuning(KeyKind kk, bool has_vals) {
   if (words == 1) {
     tn.t = 14;  // 16 Ki uint32 keys = 64 KiB of shared memory per tile
     tn.e1 = 5;  // 32 keys per thread: five layers per shared-memory round
-    tn.e2 = 4;
+    tn.e2 = 5;  // window passes: 10 layers per HBM sweep
     tn.c2 = 8;
     tn.w2 = 2;
+    tn.tma = 1;  // keys only: the bulk-copy prefetching merge measured faster
   } else if (words == 2) {
     tn.t = 13;  // 8 Ki elements of 8 bytes = 64 KiB
     tn.e1 = 4;
     tn.e2 = 4;
     tn.c2 = 8;
     tn.w2 = 2;
+    tn.tma = 0;  // key-value: the plain merge measured as fast
   } else {
     tn.t = 12;  // 4 Ki elements of 12 bytes = 48 KiB
     tn.e1 = 3;
     tn.e2 = 3;
     tn.c2 = 8;
     tn.w2 = 2;
+    tn.tma = 0;
   }
   tn.var[0] = tn.var[1] = tn.var[2] = kMelded;
   return tn;
@@ -212,7 +217,10 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
     // back, or (w2 = 2) two windows with one exchange through shared memory,
     // whose block holds 32 consecutive elements per window position so that
     // every warp access stays coalesced.
-    const int c_sm = 5;
+    // two-window passes hold 2^(c + 2*e2) elements in shared memory (no more
+    // than a tile); the c low bits of a block are consecutive elements, at
+    // least 8 of them so that every warp access fills whole 32-byte sectors
+    const int c_sm = std::max(3, std::min(5, t - 2 * e2));
     const bool two = tn.w2 >= 2 && (c_sm + 2 * e2 <= t);
     const int w_max = two ? 2 * e2 : e2;
     int hi = p - 1;
@@ -297,6 +305,17 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
     L.P.map_in = 0;
     L.P.map_out = (p == m) ? map_out : 0u;
     set_rounds(L.P, rs);
+    // single arrays: the persistent merge that streams the next tile in with
+    // bulk copies while the current one is processed (one CTA per SM)
+    size_t tma_smem = 0;
+    if (kk == KEY_U32 && tn.tma &&
+        tma_merge_kernel_u32(has_vals, e1, t, L.variant, &tma_smem).fn != nullptr &&
+        tma_smem <= smem_limit) {
+      L.tma = true;
+      L.smem = tma_smem;
+      L.P.nblocks = L.grid;
+      L.grid = std::min<uint32_t>(L.grid, uint32_t(std::max(1, g_sms_for_plans)));
+    }
     out.push_back(L);
   }
   return true;

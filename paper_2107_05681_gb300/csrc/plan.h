@@ -33,12 +33,17 @@ struct Tuning {
   int c2;     // log2 threads per block in one-round window passes
   int w2;     // register windows per window pass (1: registers only; 2: one
               // shared-memory exchange, 2*e2 layers per HBM sweep)
+  int tma = 0; // merge passes of single arrays prefetch tiles with bulk copies
   int var[3]; // variant per pass kind (used when DARM_AUTO is requested)
 };
+
+// SM count the planner sizes persistent launches for (set at init).
+extern int g_sms_for_plans;
 
 struct Launch {
   PassKind kind;
   bool fixed;  // compile-time-schedule tile/merge kernel (tile_kernel.cuh)
+  bool tma;    // persistent merge with bulk-copy prefetch (tma_merge.cuh)
   int loge;
   int variant;
   uint32_t grid;

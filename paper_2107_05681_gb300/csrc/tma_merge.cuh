@@ -1,0 +1,191 @@
+// tma_merge.cuh - persistent merge pass that prefetches the next tile with
+// the bulk-copy (TMA) engine.
+//
+// A merge pass of stage k > T runs layers T/2 .. 1 on every tile of T
+// elements.  The plain merge kernel loads a tile, processes it and stores it,
+// so an SM alternates between waiting on HBM and working on shared memory.
+// Here one CTA per SM walks over tiles (tile = blockIdx.x + i * gridDim.x):
+//   - one thread issues cp.async.bulk copies of the next tile's keys (and
+//     payload) into a dense staging buffer, completing on an mbarrier;
+//   - round 0 reads the staged tile (dense, the window's lanes are
+//     consecutive elements), runs its layers and writes the padded work
+//     buffer; the staging buffer is then free and the next tile's copy is
+//     issued at once, so it streams in while rounds 1 .. n-1 run;
+//   - the last round stores straight from registers to HBM.
+// Waits on the mbarrier are bounded (about one second of %globaltimer); if
+// one runs out the kernel latches DARM_ERR_TIMEOUT in the status word and
+// returns instead of hanging.
+#pragma once
+
+#include <type_traits>
+
+#include "tile_kernel.cuh"
+
+namespace darm {
+
+constexpr uint32_t kStatusTimeout = 7u;  // == DARM_ERR_TIMEOUT
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of the barrier for at most ~1 s.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > 1000000000ull) return false;
+  }
+}
+
+template <typename K, bool V, int LOGT>
+struct TmaMergeSmem {
+  static constexpr uint32_t kTile = 1u << LOGT;
+  static constexpr size_t kStageK = size_t(kTile) * sizeof(K);
+  static constexpr size_t kStageV = V ? size_t(kTile) * 4 : 0;
+  static constexpr size_t kWork = size_t(sizeof(K) + (V ? 4 : 0)) * smem_words(kTile);
+  static constexpr size_t kWorkOff = kStageK + kStageV;
+  static constexpr size_t kBarOff = (kWorkOff + kWork + 15) / 16 * 16;
+  static constexpr size_t kBytes = kBarOff + 16;
+};
+
+template <typename K, bool V, int LOGE, int LOGT, int VAR, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) darm_merge_tma_kernel(const __grid_constant__ PassParams P) {
+  constexpr int E = 1 << LOGE;
+  using L = TmaMergeSmem<K, V, LOGT>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  K* stage_k = reinterpret_cast<K*>(smem_raw);
+  uint32_t* stage_v = reinterpret_cast<uint32_t*>(smem_raw + L::kStageK);
+  K* sk = reinterpret_cast<K*>(smem_raw + L::kWorkOff);
+  uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + L::kWorkOff + sizeof(K) * smem_words(L::kTile));
+  const uint32_t bar = smem_addr(smem_raw + L::kBarOff);
+
+  K* __restrict__ gk = reinterpret_cast<K*>(P.keys);
+  uint32_t* __restrict__ gv = P.vals;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t ntiles = P.nblocks;
+  const uint32_t capmask = (1u << P.log2cap) - 1u;
+  const uint32_t p = P.rounds[0].p;
+  constexpr uint32_t kBytes = uint32_t(L::kStageK + L::kStageV);
+
+  uint32_t tile = blockIdx.x;
+  if (tile >= ntiles) return;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_expect_tx(bar, kBytes);
+    bulk_g2s(smem_addr(stage_k), gk + size_t(tile) * L::kTile, uint32_t(L::kStageK), bar);
+    if (V) bulk_g2s(smem_addr(stage_v), gv + size_t(tile) * L::kTile, uint32_t(L::kStageV), bar);
+  }
+
+  using SCHED = Schedule<LOGT, LOGE, true>;
+  constexpr int NR = SCHED::count;
+  K kr[E];
+  uint32_t vr[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) vr[r] = 0;
+
+  uint32_t parity = 0;
+  for (; tile < ntiles; tile += gridDim.x) {
+    if (!mbar_wait_bounded(bar, parity)) {
+      if (tid == 0 && P.status != nullptr) atomicOr(P.status, int(kStatusTimeout));
+      // give the copy in flight a last bounded chance to land before leaving
+      mbar_wait_bounded(bar, parity);
+      return;
+    }
+    parity ^= 1u;
+    const uint32_t gblk = tile << LOGT;
+    const bool asc = ((gblk & (1u << p) & capmask) == 0u);
+    const uint32_t next = tile + gridDim.x;
+
+    static_for<0, NR>([&](auto I) {
+      constexpr int IDX = decltype(I)::value;
+      constexpr SRound R = SCHED::value.r[IDX];
+      constexpr int A = R.a;
+      constexpr bool LAST = (IDX + 1 == NR);
+      const uint32_t tl = (tid & ((1u << A) - 1u)) | ((tid >> A) << (A + LOGE));
+      const uint32_t g_full = tl | gblk;
+      const uint32_t s_base = Interleave<K, V>::value ? phys8(tl) : phys(tl);
+      const uint32_t mout = LAST ? P.map_out : 0u;
+      if constexpr (IDX == 0) {
+        // from the dense staging buffer into the padded work buffer
+        auto body = [&](auto asc_c) {
+          constexpr bool ASC = decltype(asc_c)::value;
+#pragma unroll
+          for (int r = 0; r < E; ++r) {
+            const uint32_t l = tl | (uint32_t(r) << A);
+            kr[r] = stage_k[l];
+            if (V) vr[r] = stage_v[l];
+          }
+          window_side<K, V, LOGE, ASC>(kr, vr, R.cnt);
+          s_store<K, V, LOGE, A, false>(kr, vr, LAST, gk, gv, g_full, sk, sv, s_base, mout, K(0));
+        };
+        if (asc)
+          body(std::true_type{});
+        else
+          body(std::false_type{});
+        __syncthreads();
+        // the staging buffer is free: stream the next tile in behind the
+        // remaining rounds
+        if (tid == 0 && next < ntiles) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_expect_tx(bar, kBytes);
+          bulk_g2s(smem_addr(stage_k), gk + size_t(next) * L::kTile, uint32_t(L::kStageK), bar);
+          if (V) bulk_g2s(smem_addr(stage_v), gv + size_t(next) * L::kTile, uint32_t(L::kStageV), bar);
+        }
+      } else {
+        if (asc) {
+          s_load<K, V, LOGE, A, false>(kr, vr, false, gk, gv, g_full, sk, sv, s_base, 0u, K(0));
+          window_side<K, V, LOGE, true>(kr, vr, R.cnt);
+          s_store<K, V, LOGE, A, false>(kr, vr, LAST, gk, gv, g_full, sk, sv, s_base, mout, K(0));
+        } else {
+          s_load<K, V, LOGE, A, true>(kr, vr, false, gk, gv, g_full, sk, sv, s_base, 0u, K(0));
+          window_side<K, V, LOGE, false>(kr, vr, R.cnt);
+          s_store<K, V, LOGE, A, true>(kr, vr, LAST, gk, gv, g_full, sk, sv, s_base, mout, K(0));
+        }
+        __syncthreads();
+      }
+    });
+  }
+}
+
+}  // namespace darm

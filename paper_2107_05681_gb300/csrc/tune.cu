@@ -99,8 +99,10 @@ int darm_autotune(int dtype, size_t n, int has_vals, const char* db_path) {
   const int e2_cand[] = {3, 4, 5};
   for (int t : t_cand) {
     for (int e2 : e2_cand) {
-      for (int w2 = 1; w2 <= 2; ++w2) {
+      for (int w2 = 1; w2 <= 2; ++w2)
+      for (int tma = 0; tma <= base.tma; ++tma) {
         Tuning tn = base;
+        tn.tma = tma;
         tn.t = t;
         tn.e2 = e2;
         tn.w2 = w2;
@@ -140,8 +142,9 @@ int darm_autotune(int dtype, size_t n, int has_vals, const char* db_path) {
   if (db_path) {
     FILE* f = fopen(db_path, "a");
     if (!f) return DARM_ERR_INVALID_ARG;
-    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %.6f\n", int(kk), int(hv), m, best.t, best.e1,
-            best.e2, best.c2, best.w2, best.var[0], best.var[1], best.var[2], double(best_ms));
+    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %.6f\n", int(kk), int(hv), m, best.t, best.e1,
+            best.e2, best.c2, best.w2, best.tma, best.var[0], best.var[1], best.var[2],
+            double(best_ms));
     fclose(f);
   }
   return DARM_OK;
@@ -157,8 +160,8 @@ int darm_load_tune_db(const char* db_path) {
   double ms;
   int loaded = 0;
   std::lock_guard<std::mutex> lk(g_ctx.mu);
-  while (fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %lf", &kk, &hv, &m, &tn.t, &tn.e1, &tn.e2,
-                &tn.c2, &tn.w2, &tn.var[0], &tn.var[1], &tn.var[2], &ms) == 12) {
+  while (fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %lf", &kk, &hv, &m, &tn.t, &tn.e1,
+                &tn.e2, &tn.c2, &tn.w2, &tn.tma, &tn.var[0], &tn.var[1], &tn.var[2], &ms) == 13) {
     if (kk < 0 || kk > 1 || m < 0 || m > 31) continue;
     g_ctx.tuned[std::make_tuple(kk, hv, m)] = tn;
     if (m <= 16) g_ctx.tuned[std::make_tuple(kk, hv, 0)] = tn;
