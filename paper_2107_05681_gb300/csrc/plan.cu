@@ -48,14 +48,14 @@ Tuning default_tuning(KeyKind kk, bool has_vals) {
     tn.e2 = 5;  // window passes: 10 layers per HBM sweep
     tn.c2 = 8;
     tn.w2 = 2;
-    tn.tma = 1;  // keys only: the bulk-copy prefetching merge measured faster
+    tn.tma = 1;
   } else if (words == 2) {
-    tn.t = 13;  // 8 Ki elements of 8 bytes = 64 KiB
+    tn.t = 12;  // 4 Ki (key, payload) pairs = 36 KiB with padding: four CTAs per SM
     tn.e1 = 4;
     tn.e2 = 4;
     tn.c2 = 8;
     tn.w2 = 2;
-    tn.tma = 0;  // key-value: the plain merge measured as fast
+    tn.tma = 1;
   } else {
     tn.t = 12;  // 4 Ki elements of 12 bytes = 48 KiB
     tn.e1 = 3;
@@ -314,7 +314,15 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
       L.tma = true;
       L.smem = tma_smem;
       L.P.nblocks = L.grid;
-      L.grid = std::min<uint32_t>(L.grid, uint32_t(std::max(1, g_sms_for_plans)));
+      int per_sm = 1;
+      const void* tfn = tma_merge_kernel_u32(has_vals, e1, t, L.variant, nullptr).fn;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tfn, int(L.threads), L.smem) !=
+              cudaSuccess ||
+          per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+      }
+      L.grid = std::min<uint32_t>(L.grid, uint32_t(std::max(1, g_sms_for_plans) * per_sm));
     }
     out.push_back(L);
   }

@@ -25,11 +25,11 @@ struct Combo {
   int loge, logt;
 };
 constexpr Combo kCombos[] = {{false, 4, 12}, {false, 4, 13}, {false, 4, 14}, {true, 4, 12},
-                             {true, 4, 13}, {true, 5, 13}, {false, 5, 14}};
+                             {true, 4, 13}, {true, 5, 13}, {false, 5, 14}, {false, 5, 13}};
 
 template <bool V, int LOGE, int LOGT, int VAR>
 KernelEntry mentry() {
-  constexpr int MT = 1 << (LOGT - LOGE);  // one CTA per SM: up to 128 registers
+  constexpr int MT = 1 << (LOGT - LOGE);
   return KernelEntry{
       reinterpret_cast<const void*>(&darm_merge_tma_kernel<uint32_t, V, LOGE, LOGT, VAR, MT>), MT};
 }
@@ -37,9 +37,17 @@ KernelEntry mentry() {
 }  // namespace
 
 KernelEntry tma_merge_kernel_u32(bool has_vals, int loge, int logt, int var, size_t* smem_bytes) {
+  if (has_vals && loge == 4 && logt == 12) {
+    if (smem_bytes) *smem_bytes = TmaMergeSmem<uint32_t, true, 12>::kBytes;
+    return var ? mentry<true, 4, 12, 1>() : mentry<true, 4, 12, 0>();
+  }
   if (has_vals && loge == 4 && logt == 13) {
     if (smem_bytes) *smem_bytes = TmaMergeSmem<uint32_t, true, 13>::kBytes;
     return var ? mentry<true, 4, 13, 1>() : mentry<true, 4, 13, 0>();
+  }
+  if (!has_vals && loge == 5 && logt == 13) {
+    if (smem_bytes) *smem_bytes = TmaMergeSmem<uint32_t, false, 13>::kBytes;
+    return var ? mentry<false, 5, 13, 1>() : mentry<false, 5, 13, 0>();
   }
   if (!has_vals && loge == 5 && logt == 14) {
     if (smem_bytes) *smem_bytes = TmaMergeSmem<uint32_t, false, 14>::kBytes;
@@ -50,10 +58,10 @@ KernelEntry tma_merge_kernel_u32(bool has_vals, int loge, int logt, int var, siz
 
 void for_each_tma_kernel_u32(void (*fn)(const void*, void*), void* ctx) {
   for (int var = 0; var < 2; ++var) {
-    KernelEntry a = tma_merge_kernel_u32(true, 4, 13, var, nullptr);
-    KernelEntry b = tma_merge_kernel_u32(false, 5, 14, var, nullptr);
-    fn(a.fn, ctx);
-    fn(b.fn, ctx);
+    fn(tma_merge_kernel_u32(true, 4, 12, var, nullptr).fn, ctx);
+    fn(tma_merge_kernel_u32(true, 4, 13, var, nullptr).fn, ctx);
+    fn(tma_merge_kernel_u32(false, 5, 13, var, nullptr).fn, ctx);
+    fn(tma_merge_kernel_u32(false, 5, 14, var, nullptr).fn, ctx);
   }
 }
 
@@ -65,6 +73,7 @@ KernelEntry tile_kernel_u32(bool has_vals, int loge, int logt, int var, bool mer
   if (has_vals && loge == 4 && logt == 13) return tpick<true, 4, 13>(var, merge);
   if (has_vals && loge == 5 && logt == 13) return tpick<true, 5, 13>(var, merge);
   if (!has_vals && loge == 5 && logt == 14) return tpick<false, 5, 14>(var, merge);
+  if (!has_vals && loge == 5 && logt == 13) return tpick<false, 5, 13>(var, merge);
   return KernelEntry{nullptr, 0};
 }
 

@@ -85,8 +85,10 @@ struct TmaMergeSmem {
   static constexpr size_t kBytes = kBarOff + 16;
 };
 
+// Block size MAXT = threads of one tile; small tiles ask for 64 registers so
+// that several CTAs share an SM.
 template <typename K, bool V, int LOGE, int LOGT, int VAR, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) darm_merge_tma_kernel(const __grid_constant__ PassParams P) {
+__global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_kernel(const __grid_constant__ PassParams P) {
   constexpr int E = 1 << LOGE;
   using L = TmaMergeSmem<K, V, LOGT>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
