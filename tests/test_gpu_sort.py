@@ -158,3 +158,20 @@ def test_launch_counter_counts_kernels(darm):
     passes, launches, _ = darm.plan_info(darm.U32, 1 << 20, False)
     assert darm.launch_count() - before == launches
     assert darm.device_status() == darm.OK
+
+
+def test_autotune_then_auto_variant(darm, tmp_path):
+    """The tuner's choice (tile size, window depth, form per pass kind) is
+    persisted, reloaded and gives the same bit-exact result."""
+    db = str(tmp_path / "tune.db")
+    n = 1 << 18
+    darm.autotune(darm.U32, n, True, db)
+    lines = open(db).read().split("\n")
+    assert len([ln for ln in lines if ln.strip()]) == 1
+    darm.load_tune_db(db)
+    keys = synth.uniform_u32(61, n) % np.uint32(1000)
+    vals = np.arange(n, dtype=np.uint32)
+    ek, ev = oracle.bitonic_sort(keys, vals)
+    gk, gv = gpu_sort(darm, keys, vals, variant="auto")
+    assert_equal("keys", gk, ek)
+    assert_equal("payload", gv, ev)
