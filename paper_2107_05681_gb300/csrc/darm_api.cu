@@ -41,7 +41,9 @@ int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_
     P.vals = vals;
     P.status = g_ctx.d_status;
     const void* fn =
-        L.tma ? tma_merge_kernel_u32(has_vals, L.loge, int(L.P.b), L.variant, nullptr).fn
+        L.win2 ? ((kk == KEY_U32) ? window2_kernel_u32(has_vals, L.loge, int(L.P.c), L.variant)
+                                  : window2_kernel_u64(has_vals, L.loge, int(L.P.c), L.variant)).fn
+        : L.tma ? tma_merge_kernel_u32(has_vals, L.loge, int(L.P.b), L.variant, nullptr).fn
         : L.fixed ? fixed_kernel_fn(kk, has_vals, L.loge, int(L.P.b), L.variant, L.kind == PASS_MERGE)
                   : kernel_fn(kk, has_vals, L.loge, L.variant);
     if (!fn) return DARM_ERR_INVALID_ARG;
@@ -147,6 +149,7 @@ int darm_sort_init(int device, size_t workspace_bytes) {
   for_each_tile_kernel_u32(set_smem_attr, st);
   for_each_tile_kernel_u64(set_smem_attr, st);
   for_each_tma_kernel_u32(set_smem_attr, st);
+  for_each_window2_kernel(set_smem_attr, st);
   if (st[1] != 0) {
     fprintf(stderr, "darm: configuring shared memory failed: %s\n",
             cudaGetErrorString(cudaError_t(st[1])));

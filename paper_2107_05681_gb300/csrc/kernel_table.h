@@ -25,6 +25,11 @@ KernelEntry tile_kernel_u64(bool has_vals, int loge, int logt, int var, bool mer
 // (tma_merge.cuh); smem_bytes receives the dynamic shared memory they need.
 KernelEntry tma_merge_kernel_u32(bool has_vals, int loge, int logt, int var, size_t* smem_bytes);
 
+// Two-window passes with a compile-time shape (window2_kernel.cuh): E =
+// 2^loge, c low consecutive-element bits.
+KernelEntry window2_kernel_u32(bool has_vals, int loge, int c, int var);
+KernelEntry window2_kernel_u64(bool has_vals, int loge, int c, int var);
+
 // Call fn(kernel address, ctx) for every instantiation (used to configure
 // shared-memory limits once per device).
 void for_each_kernel_u32(void (*fn)(const void*, void*), void* ctx);
@@ -32,5 +37,6 @@ void for_each_kernel_u64(void (*fn)(const void*, void*), void* ctx);
 void for_each_tile_kernel_u32(void (*fn)(const void*, void*), void* ctx);
 void for_each_tile_kernel_u64(void (*fn)(const void*, void*), void* ctx);
 void for_each_tma_kernel_u32(void (*fn)(const void*, void*), void* ctx);
+void for_each_window2_kernel(void (*fn)(const void*, void*), void* ctx);
 
 }  // namespace darm

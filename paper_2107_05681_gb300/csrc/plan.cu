@@ -282,6 +282,9 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
           rs.push_back(r);
         }
         set_rounds(L.P, rs);
+        KernelEntry w2e = (kk == KEY_U32) ? window2_kernel_u32(has_vals, e2, c, L.variant)
+                                          : window2_kernel_u64(has_vals, e2, c, L.variant);
+        L.win2 = (nr == 2 && w2e.fn != nullptr && int(L.threads) == w2e.max_threads);
       }
       out.push_back(L);
       hi = lo - 1;

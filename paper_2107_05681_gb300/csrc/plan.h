@@ -44,6 +44,7 @@ struct Launch {
   PassKind kind;
   bool fixed;  // compile-time-schedule tile/merge kernel (tile_kernel.cuh)
   bool tma;    // persistent merge with bulk-copy prefetch (tma_merge.cuh)
+  bool win2;   // two-window pass with a compile-time shape (window2_kernel.cuh)
   int loge;
   int variant;
   uint32_t grid;
