@@ -23,7 +23,8 @@ KernelEntry tile_kernel_u64(bool has_vals, int loge, int logt, int var, bool mer
 
 // Persistent merge kernels that prefetch tiles with bulk copies
 // (tma_merge.cuh); smem_bytes receives the dynamic shared memory they need.
-KernelEntry tma_merge_kernel_u32(bool has_vals, int loge, int logt, int var, size_t* smem_bytes);
+KernelEntry tma_merge_kernel_u32(bool has_vals, int loge, int logt, int ns, int var,
+                                 size_t* smem_bytes);
 
 // Two-window passes with a compile-time shape (window2_kernel.cuh): E =
 // 2^loge, c low consecutive-element bits.

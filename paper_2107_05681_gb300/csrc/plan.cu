@@ -48,7 +48,7 @@ Tuning default_tuning(KeyKind kk, bool has_vals) {
     tn.e2 = 5;  // window passes: 10 layers per HBM sweep
     tn.c2 = 8;
     tn.w2 = 2;
-    tn.tma = 1;
+    tn.tma = 2;  // two tiles stream in while one is merged (200 KiB per SM)
   } else if (words == 2) {
     tn.t = 12;  // 4 Ki (key, payload) pairs = 36 KiB with padding: four CTAs per SM
     tn.e1 = 4;
@@ -312,13 +312,13 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
     // bulk copies while the current one is processed (one CTA per SM)
     size_t tma_smem = 0;
     if (kk == KEY_U32 && tn.tma &&
-        tma_merge_kernel_u32(has_vals, e1, t, L.variant, &tma_smem).fn != nullptr &&
+        tma_merge_kernel_u32(has_vals, e1, t, tn.tma, L.variant, &tma_smem).fn != nullptr &&
         tma_smem <= smem_limit) {
-      L.tma = true;
+      L.tma = tn.tma;
       L.smem = tma_smem;
       L.P.nblocks = L.grid;
       int per_sm = 1;
-      const void* tfn = tma_merge_kernel_u32(has_vals, e1, t, L.variant, nullptr).fn;
+      const void* tfn = tma_merge_kernel_u32(has_vals, e1, t, tn.tma, L.variant, nullptr).fn;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tfn, int(L.threads), L.smem) !=
               cudaSuccess ||
           per_sm < 1) {

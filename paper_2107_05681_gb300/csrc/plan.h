@@ -34,6 +34,7 @@ struct Tuning {
   int w2;     // register windows per window pass (1: registers only; 2: one
               // shared-memory exchange, 2*e2 layers per HBM sweep)
   int tma = 0; // merge passes of single arrays prefetch tiles with bulk copies
+               // into this many staging buffers (0: plain merge kernel)
   int var[3]; // variant per pass kind (used when DARM_AUTO is requested)
 };
 
@@ -43,7 +44,8 @@ extern int g_sms_for_plans;
 struct Launch {
   PassKind kind;
   bool fixed;  // compile-time-schedule tile/merge kernel (tile_kernel.cuh)
-  bool tma;    // persistent merge with bulk-copy prefetch (tma_merge.cuh)
+  int tma;     // persistent merge with bulk-copy prefetch into this many
+               // staging buffers (tma_merge.cuh); 0: plain merge kernel
   bool win2;   // two-window pass with a compile-time shape (window2_kernel.cuh)
   int loge;
   int variant;

@@ -109,6 +109,21 @@ __device__ __forceinline__ void static_for(F&& f) {
   }
 }
 
+// 256-bit global stores (sm_100 and later): a thread that owns eight or
+// more consecutive 32-bit words writes them as whole 32-byte sectors, so no
+// sector of a warp's store is written in two halves by two instructions.
+// The address must be 32-byte aligned; callers fall back to 128-bit stores
+// otherwise.
+__device__ __forceinline__ bool aligned32(const void* p) {
+  return (reinterpret_cast<uintptr_t>(p) & 31u) == 0;
+}
+
+__device__ __forceinline__ void st_global_v8(void* p, const uint32_t (&w)[8]) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w[0]),
+               "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+               : "memory");
+}
+
 // Key-value tiles with 32-bit keys keep each (key, payload) pair together in
 // one 8-byte shared-memory slot, so one 64-bit access moves both.  Pair l
 // lives at slot phys8(l) = l + 2 * (l / 16): two pad slots after every 16
@@ -221,7 +236,7 @@ __device__ __forceinline__ void s_load(K (&kr)[1 << LOGE], uint32_t (&vr)[1 << L
   }
 }
 
-template <typename K, bool V, int LOGE, int A, bool REV>
+template <typename K, bool V, int LOGE, int A, bool REV, bool WIDE = false>
 __device__ __forceinline__ void s_store(const K (&kr)[1 << LOGE], const uint32_t (&vr)[1 << LOGE],
                                         bool to_global, K* __restrict__ gk, uint32_t* __restrict__ gv,
                                         uint32_t g_t, K* sk, uint32_t* sv, uint32_t s_base,
@@ -229,6 +244,24 @@ __device__ __forceinline__ void s_store(const K (&kr)[1 << LOGE], const uint32_t
   constexpr int E = 1 << LOGE;
   constexpr int KPV = 16 / sizeof(K);
   if (to_global) {
+    if constexpr (WIDE && A == 0 && sizeof(K) == 4 && E >= 8) {
+      if (aligned32(gk + g_t) && (!V || aligned32(gv + g_t))) {
+#pragma unroll
+        for (int q0 = 0; q0 < E / 8; ++q0) {
+          const int q = REV ? (E / 8 - 1 - q0) : q0;
+          uint32_t w[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) w[u] = uint32_t(key_out<K>(kr[q * 8 + u] ^ m, mapf));
+          st_global_v8(gk + g_t + q * 8, w);
+          if constexpr (V) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) w[u] = vr[q * 8 + u];
+            st_global_v8(gv + g_t + q * 8, w);
+          }
+        }
+        return;
+      }
+    }
     if constexpr (A == 0 && E >= KPV) {
 #pragma unroll
       for (int q0 = 0; q0 < E / KPV; ++q0) {
@@ -459,8 +492,12 @@ __device__ __forceinline__ void tile_block(const PassParams& P, uint32_t bidx, K
   });
 }
 
+// Resident CTAs asked of the compiler for a tile kernel of MAXT threads: a
+// 256-thread tile may use 85 registers (three CTAs per SM), larger ones 64.
+constexpr int tile_min_blocks(int maxt) { return maxt >= 1024 ? 1 : (maxt >= 512 ? 2 : 3); }
+
 template <typename K, bool V, int LOGE, int LOGT, int VAR, bool MERGE, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) darm_tile_kernel(const __grid_constant__ PassParams P) {
+__global__ void __launch_bounds__(MAXT, tile_min_blocks(MAXT)) darm_tile_kernel(const __grid_constant__ PassParams P) {
   constexpr uint32_t SW = smem_words(1u << LOGT);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   K* sk = reinterpret_cast<K*>(smem_raw);

@@ -1,14 +1,13 @@
 // tile_u32.cu - compile-time-schedule tile and merge kernels for uint32_t keys.
 #include "kernel_table.h"
 #include "tile_kernel.cuh"
-#include "tma_merge.cuh"
 
 namespace darm {
 namespace {
 
 template <bool V, int LOGE, int LOGT, int VAR, bool MERGE>
 KernelEntry tentry() {
-  constexpr int MT = max_threads_for<uint32_t, V, LOGE>();
+  constexpr int MT = 1 << (LOGT - LOGE);  // one tile per CTA
   static_assert((1 << (LOGT - LOGE)) <= MT, "tile too large for the block size");
   return KernelEntry{
       reinterpret_cast<const void*>(&darm_tile_kernel<uint32_t, V, LOGE, LOGT, VAR, MERGE, MT>), MT};
@@ -27,43 +26,7 @@ struct Combo {
 constexpr Combo kCombos[] = {{false, 4, 12}, {false, 4, 13}, {false, 4, 14}, {true, 4, 12},
                              {true, 4, 13}, {true, 5, 13}, {false, 5, 14}, {false, 5, 13}};
 
-template <bool V, int LOGE, int LOGT, int VAR>
-KernelEntry mentry() {
-  constexpr int MT = 1 << (LOGT - LOGE);
-  return KernelEntry{
-      reinterpret_cast<const void*>(&darm_merge_tma_kernel<uint32_t, V, LOGE, LOGT, VAR, MT>), MT};
-}
-
 }  // namespace
-
-KernelEntry tma_merge_kernel_u32(bool has_vals, int loge, int logt, int var, size_t* smem_bytes) {
-  if (has_vals && loge == 4 && logt == 12) {
-    if (smem_bytes) *smem_bytes = TmaMergeSmem<uint32_t, true, 12>::kBytes;
-    return var ? mentry<true, 4, 12, 1>() : mentry<true, 4, 12, 0>();
-  }
-  if (has_vals && loge == 4 && logt == 13) {
-    if (smem_bytes) *smem_bytes = TmaMergeSmem<uint32_t, true, 13>::kBytes;
-    return var ? mentry<true, 4, 13, 1>() : mentry<true, 4, 13, 0>();
-  }
-  if (!has_vals && loge == 5 && logt == 13) {
-    if (smem_bytes) *smem_bytes = TmaMergeSmem<uint32_t, false, 13>::kBytes;
-    return var ? mentry<false, 5, 13, 1>() : mentry<false, 5, 13, 0>();
-  }
-  if (!has_vals && loge == 5 && logt == 14) {
-    if (smem_bytes) *smem_bytes = TmaMergeSmem<uint32_t, false, 14>::kBytes;
-    return var ? mentry<false, 5, 14, 1>() : mentry<false, 5, 14, 0>();
-  }
-  return KernelEntry{nullptr, 0};
-}
-
-void for_each_tma_kernel_u32(void (*fn)(const void*, void*), void* ctx) {
-  for (int var = 0; var < 2; ++var) {
-    fn(tma_merge_kernel_u32(true, 4, 12, var, nullptr).fn, ctx);
-    fn(tma_merge_kernel_u32(true, 4, 13, var, nullptr).fn, ctx);
-    fn(tma_merge_kernel_u32(false, 5, 13, var, nullptr).fn, ctx);
-    fn(tma_merge_kernel_u32(false, 5, 14, var, nullptr).fn, ctx);
-  }
-}
 
 KernelEntry tile_kernel_u32(bool has_vals, int loge, int logt, int var, bool merge) {
   if (!has_vals && loge == 4 && logt == 12) return tpick<false, 4, 12>(var, merge);

@@ -7,7 +7,7 @@ namespace {
 
 template <bool V, int LOGE, int LOGT, int VAR, bool MERGE>
 KernelEntry tentry() {
-  constexpr int MT = max_threads_for<uint64_t, V, LOGE>();
+  constexpr int MT = 1 << (LOGT - LOGE);  // one tile per CTA
   static_assert((1 << (LOGT - LOGE)) <= MT, "tile too large for the block size");
   return KernelEntry{
       reinterpret_cast<const void*>(&darm_tile_kernel<uint64_t, V, LOGE, LOGT, VAR, MERGE, MT>), MT};

@@ -1,20 +1,24 @@
-// tma_merge.cuh - persistent merge pass that prefetches the next tile with
-// the bulk-copy (TMA) engine.
+// tma_merge.cuh - persistent merge pass that prefetches tiles with the
+// bulk-copy (TMA) engine.
 //
 // A merge pass of stage k > T runs layers T/2 .. 1 on every tile of T
 // elements.  The plain merge kernel loads a tile, processes it and stores it,
 // so an SM alternates between waiting on HBM and working on shared memory.
-// Here one CTA per SM walks over tiles (tile = blockIdx.x + i * gridDim.x):
-//   - one thread issues cp.async.bulk copies of the next tile's keys (and
-//     payload) into a dense staging buffer, completing on an mbarrier;
+// Here one CTA per SM (or a few) walks over tiles
+// (tile = blockIdx.x + i * gridDim.x) with NS dense staging buffers:
+//   - one thread issues cp.async.bulk copies of a tile's keys (and payload)
+//     into a free staging buffer, completing on that buffer's mbarrier;
 //   - round 0 reads the staged tile (dense, the window's lanes are
 //     consecutive elements), runs its layers and writes the padded work
-//     buffer; the staging buffer is then free and the next tile's copy is
-//     issued at once, so it streams in while rounds 1 .. n-1 run;
-//   - the last round stores straight from registers to HBM.
-// Waits on the mbarrier are bounded (about one second of %globaltimer); if
-// one runs out the kernel latches DARM_ERR_TIMEOUT in the status word and
-// returns instead of hanging.
+//     buffer; the staging buffer is then free and the copy of the tile NS
+//     steps ahead is issued at once, so NS tiles stream in while rounds
+//     1 .. n-1 run;
+//   - the last round stores straight from registers to HBM, in 256-bit
+//     stores where the address allows.
+// Waits on an mbarrier are bounded (about one second of %globaltimer); if one
+// runs out the kernel latches DARM_ERR_TIMEOUT in the status word, waits
+// (bounded again) for the copies it still has in flight and returns instead
+// of hanging.
 #pragma once
 
 #include <type_traits>
@@ -74,29 +78,29 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
   }
 }
 
-template <typename K, bool V, int LOGT>
+template <typename K, bool V, int LOGT, int NS>
 struct TmaMergeSmem {
   static constexpr uint32_t kTile = 1u << LOGT;
   static constexpr size_t kStageK = size_t(kTile) * sizeof(K);
   static constexpr size_t kStageV = V ? size_t(kTile) * 4 : 0;
+  static constexpr size_t kStage = kStageK + kStageV;  // one staging buffer
   static constexpr size_t kWork = size_t(sizeof(K) + (V ? 4 : 0)) * smem_words(kTile);
-  static constexpr size_t kWorkOff = kStageK + kStageV;
+  static constexpr size_t kWorkOff = NS * kStage;
   static constexpr size_t kBarOff = (kWorkOff + kWork + 15) / 16 * 16;
-  static constexpr size_t kBytes = kBarOff + 16;
+  static constexpr size_t kBytes = kBarOff + 8 * NS;
 };
 
 // Block size MAXT = threads of one tile; small tiles ask for 64 registers so
 // that several CTAs share an SM.
-template <typename K, bool V, int LOGE, int LOGT, int VAR, int MAXT>
+template <typename K, bool V, int LOGE, int LOGT, int NS, int VAR, int MAXT>
 __global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_kernel(const __grid_constant__ PassParams P) {
+  static_assert(NS >= 1 && NS <= 4, "one to four staging buffers");
   constexpr int E = 1 << LOGE;
-  using L = TmaMergeSmem<K, V, LOGT>;
+  using L = TmaMergeSmem<K, V, LOGT, NS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  K* stage_k = reinterpret_cast<K*>(smem_raw);
-  uint32_t* stage_v = reinterpret_cast<uint32_t*>(smem_raw + L::kStageK);
   K* sk = reinterpret_cast<K*>(smem_raw + L::kWorkOff);
   uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + L::kWorkOff + sizeof(K) * smem_words(L::kTile));
-  const uint32_t bar = smem_addr(smem_raw + L::kBarOff);
+  const uint32_t bar0 = smem_addr(smem_raw + L::kBarOff);
 
   K* __restrict__ gk = reinterpret_cast<K*>(P.keys);
   uint32_t* __restrict__ gv = P.vals;
@@ -104,19 +108,36 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_ke
   const uint32_t ntiles = P.nblocks;
   const uint32_t capmask = (1u << P.log2cap) - 1u;
   const uint32_t p = P.rounds[0].p;
-  constexpr uint32_t kBytes = uint32_t(L::kStageK + L::kStageV);
+  constexpr uint32_t kBytes = uint32_t(L::kStage);
+
+  // copy tile `tl` into staging buffer `b` (thread 0 only)
+  auto issue = [&](uint32_t tl, int b) {
+    const uint32_t bar = bar0 + 8u * uint32_t(b);
+    unsigned char* st = smem_raw + size_t(b) * L::kStage;
+    mbar_expect_tx(bar, kBytes);
+    bulk_g2s(smem_addr(st), gk + size_t(tl) * L::kTile, uint32_t(L::kStageK), bar);
+    if (V) bulk_g2s(smem_addr(st + L::kStageK), gv + size_t(tl) * L::kTile, uint32_t(L::kStageV), bar);
+  };
 
   uint32_t tile = blockIdx.x;
   if (tile >= ntiles) return;
   if (tid == 0) {
-    mbar_init(bar, 1);
+#pragma unroll
+    for (int b = 0; b < NS; ++b) mbar_init(bar0 + 8u * uint32_t(b), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (tid == 0) {
-    mbar_expect_tx(bar, kBytes);
-    bulk_g2s(smem_addr(stage_k), gk + size_t(tile) * L::kTile, uint32_t(L::kStageK), bar);
-    if (V) bulk_g2s(smem_addr(stage_v), gv + size_t(tile) * L::kTile, uint32_t(L::kStageV), bar);
+  // Every thread keeps the same account of which buffers have a copy in
+  // flight (bit b of `pending`) and of each barrier's phase (bit b of
+  // `phase`), so that a timed-out wait can drain them.
+  uint32_t pending = 0;
+#pragma unroll
+  for (int b = 0; b < NS; ++b) {
+    const uint32_t tl = tile + uint32_t(b) * gridDim.x;
+    if (tl < ntiles) {
+      if (tid == 0) issue(tl, b);
+      pending |= 1u << b;
+    }
   }
 
   using SCHED = Schedule<LOGT, LOGE, true>;
@@ -126,18 +147,25 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_ke
 #pragma unroll
   for (int r = 0; r < E; ++r) vr[r] = 0;
 
-  uint32_t parity = 0;
+  uint32_t phase = 0;
+  int b = 0;
   for (; tile < ntiles; tile += gridDim.x) {
-    if (!mbar_wait_bounded(bar, parity)) {
+    const uint32_t bar = bar0 + 8u * uint32_t(b);
+    if (!mbar_wait_bounded(bar, (phase >> b) & 1u)) {
       if (tid == 0 && P.status != nullptr) atomicOr(P.status, int(kStatusTimeout));
-      // give the copy in flight a last bounded chance to land before leaving
-      mbar_wait_bounded(bar, parity);
+      // give every copy in flight a last bounded chance to land before leaving
+#pragma unroll
+      for (int q = 0; q < NS; ++q)
+        if ((pending >> q) & 1u) mbar_wait_bounded(bar0 + 8u * uint32_t(q), (phase >> q) & 1u);
       return;
     }
-    parity ^= 1u;
+    phase ^= 1u << b;
+    pending &= ~(1u << b);
+    const K* stage_k = reinterpret_cast<const K*>(smem_raw + size_t(b) * L::kStage);
+    const uint32_t* stage_v = reinterpret_cast<const uint32_t*>(smem_raw + size_t(b) * L::kStage + L::kStageK);
     const uint32_t gblk = tile << LOGT;
     const bool asc = ((gblk & (1u << p) & capmask) == 0u);
-    const uint32_t next = tile + gridDim.x;
+    const uint32_t next = tile + uint32_t(NS) * gridDim.x;
 
     static_for<0, NR>([&](auto I) {
       constexpr int IDX = decltype(I)::value;
@@ -159,34 +187,36 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_ke
             if (V) vr[r] = stage_v[l];
           }
           window_side<K, V, LOGE, ASC>(kr, vr, R.cnt);
-          s_store<K, V, LOGE, A, false>(kr, vr, LAST, gk, gv, g_full, sk, sv, s_base, mout, K(0));
+          s_store<K, V, LOGE, A, false, true>(kr, vr, LAST, gk, gv, g_full, sk, sv, s_base, mout, K(0));
         };
         if (asc)
           body(std::true_type{});
         else
           body(std::false_type{});
         __syncthreads();
-        // the staging buffer is free: stream the next tile in behind the
-        // remaining rounds
-        if (tid == 0 && next < ntiles) {
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          mbar_expect_tx(bar, kBytes);
-          bulk_g2s(smem_addr(stage_k), gk + size_t(next) * L::kTile, uint32_t(L::kStageK), bar);
-          if (V) bulk_g2s(smem_addr(stage_v), gv + size_t(next) * L::kTile, uint32_t(L::kStageV), bar);
+        // the staging buffer is free: stream the tile NS steps ahead in
+        // behind the remaining rounds
+        if (next < ntiles) {
+          if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(next, b);
+          }
+          pending |= 1u << b;
         }
       } else {
         if (asc) {
           s_load<K, V, LOGE, A, false>(kr, vr, false, gk, gv, g_full, sk, sv, s_base, 0u, K(0));
           window_side<K, V, LOGE, true>(kr, vr, R.cnt);
-          s_store<K, V, LOGE, A, false>(kr, vr, LAST, gk, gv, g_full, sk, sv, s_base, mout, K(0));
+          s_store<K, V, LOGE, A, false, true>(kr, vr, LAST, gk, gv, g_full, sk, sv, s_base, mout, K(0));
         } else {
           s_load<K, V, LOGE, A, true>(kr, vr, false, gk, gv, g_full, sk, sv, s_base, 0u, K(0));
           window_side<K, V, LOGE, false>(kr, vr, R.cnt);
-          s_store<K, V, LOGE, A, true>(kr, vr, LAST, gk, gv, g_full, sk, sv, s_base, mout, K(0));
+          s_store<K, V, LOGE, A, true, true>(kr, vr, LAST, gk, gv, g_full, sk, sv, s_base, mout, K(0));
         }
         __syncthreads();
       }
     });
+    b = (b + 1 == NS) ? 0 : b + 1;
   }
 }
 

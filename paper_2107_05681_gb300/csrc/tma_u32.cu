@@ -1,0 +1,48 @@
+// tma_u32.cu - instantiations of the bulk-copy-prefetching merge pass for
+// uint32_t keys (tma_merge.cuh).
+#include "kernel_table.h"
+#include "tma_merge.cuh"
+
+namespace darm {
+namespace {
+
+template <bool V, int LOGE, int LOGT, int NS>
+KernelEntry mentry(int var, size_t* smem_bytes) {
+  constexpr int MT = 1 << (LOGT - LOGE);
+  if (smem_bytes) *smem_bytes = TmaMergeSmem<uint32_t, V, LOGT, NS>::kBytes;
+  if (var)
+    return KernelEntry{
+        reinterpret_cast<const void*>(&darm_merge_tma_kernel<uint32_t, V, LOGE, LOGT, NS, 1, MT>), MT};
+  return KernelEntry{
+      reinterpret_cast<const void*>(&darm_merge_tma_kernel<uint32_t, V, LOGE, LOGT, NS, 0, MT>), MT};
+}
+
+template <bool V, int LOGE, int LOGT>
+KernelEntry mpick(int ns, int var, size_t* smem_bytes) {
+  if (ns == 1) return mentry<V, LOGE, LOGT, 1>(var, smem_bytes);
+  if (ns == 2) return mentry<V, LOGE, LOGT, 2>(var, smem_bytes);
+  return KernelEntry{nullptr, 0};
+}
+
+}  // namespace
+
+KernelEntry tma_merge_kernel_u32(bool has_vals, int loge, int logt, int ns, int var,
+                                 size_t* smem_bytes) {
+  if (has_vals && loge == 4 && logt == 12) return mpick<true, 4, 12>(ns, var, smem_bytes);
+  if (has_vals && loge == 4 && logt == 13) return mpick<true, 4, 13>(ns, var, smem_bytes);
+  if (!has_vals && loge == 5 && logt == 13) return mpick<false, 5, 13>(ns, var, smem_bytes);
+  if (!has_vals && loge == 5 && logt == 14) return mpick<false, 5, 14>(ns, var, smem_bytes);
+  return KernelEntry{nullptr, 0};
+}
+
+void for_each_tma_kernel_u32(void (*fn)(const void*, void*), void* ctx) {
+  for (int var = 0; var < 2; ++var)
+    for (int ns = 1; ns <= 2; ++ns) {
+      fn(tma_merge_kernel_u32(true, 4, 12, ns, var, nullptr).fn, ctx);
+      fn(tma_merge_kernel_u32(true, 4, 13, ns, var, nullptr).fn, ctx);
+      fn(tma_merge_kernel_u32(false, 5, 13, ns, var, nullptr).fn, ctx);
+      fn(tma_merge_kernel_u32(false, 5, 14, ns, var, nullptr).fn, ctx);
+    }
+}
+
+}  // namespace darm

@@ -100,7 +100,7 @@ int darm_autotune(int dtype, size_t n, int has_vals, const char* db_path) {
   for (int t : t_cand) {
     for (int e2 : e2_cand) {
       for (int w2 = 1; w2 <= 2; ++w2)
-      for (int tma = 0; tma <= base.tma; ++tma) {
+      for (int tma = 0; tma <= 2; ++tma) {
         Tuning tn = base;
         tn.tma = tma;
         tn.t = t;
