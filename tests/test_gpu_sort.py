@@ -43,7 +43,7 @@ def test_u32_kv_all_sizes(darm, m, desc, variant):
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
-@pytest.mark.parametrize("m", [1, 2, 5, 9, 13, 14, 15, 17, 19])
+@pytest.mark.parametrize("m", [1, 2, 5, 9, 13, 14, 15, 17, 19, 21])
 def test_u32_keys_only(darm, m, variant):
     n = 1 << m
     keys = synth.uniform_u32(2000 + m, n)
@@ -72,6 +72,30 @@ def test_f32_total_order(darm, m, variant):
     for desc in (False, True):
         _check(darm, x, None, desc, variant)
         _check(darm, x, np.arange(n, dtype=np.uint32), desc, variant)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_buffers_16_byte_aligned_only(darm, variant):
+    """Key and payload pointers 16 bytes past a 256-byte boundary: the merge
+    pass's 256-bit stores must fall back to 128-bit ones and the result stay
+    exact."""
+    import torch
+
+    n = 1 << 17
+    keys = synth.uniform_u32(91, n) % np.uint32(1 << 12)
+    vals = np.arange(n, dtype=np.uint32)
+    ek, ev = oracle.bitonic_sort(keys, vals)
+    pad = np.zeros(4, dtype=np.uint32)
+    kb = torch.from_numpy(np.concatenate([pad, keys])).cuda()
+    vb = torch.from_numpy(np.concatenate([pad, vals])).cuda()
+    K, V = kb[4:], vb[4:]
+    assert K.data_ptr() % 32 == 16 and V.data_ptr() % 32 == 16
+    darm.sort(K, V, variant=variant)
+    torch.cuda.synchronize()
+    kh, vh = kb.cpu().numpy(), vb.cpu().numpy()
+    assert_equal("keys", kh[4:], ek)
+    assert_equal("payload", vh[4:], ev)
+    assert not kh[:4].any() and not vh[:4].any()
 
 
 def test_cross_variant_identity(darm):
