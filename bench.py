@@ -250,7 +250,25 @@ def run_segmented(args, world, rank, local):
     stream = torch.cuda.current_stream()
     out = {}
     launches = 0
-    for variant in ("melded", "divergent"):
+    tuned = None
+    for variant in ("melded", "divergent", "auto"):
+        if variant == "auto":
+            # the batch autotuner (outside the timed region) picks tile size,
+            # window depth and the form per pass kind for this layout
+            import tempfile
+            with tempfile.TemporaryDirectory() as td:
+                db = os.path.join(td, "seg.db")
+                k.copy_(src_k)
+                v.copy_(src_v)
+                darm.autotune_segmented(k, v, segs.offsets, segs.lengths, db)
+                f = open(db).read().split()
+            names = ["key_kind", "payload", "log2n", "tile_log2", "e_tile_log2", "e_window_log2",
+                     "window_threads_log2", "windows_per_pass", "bulk_copy_buffers",
+                     "form_tile", "form_window", "form_merge"]
+            tuned = dict(zip(names, (int(x) for x in f[:12])))
+            for kf in ("form_tile", "form_window", "form_merge"):
+                tuned[kf] = "melded" if tuned[kf] == 1 else "divergent"
+            tuned["tuner_ms"] = float(f[12])
         for _ in range(args.warmup):
             k.copy_(src_k)
             v.copy_(src_v)
@@ -286,6 +304,8 @@ def run_segmented(args, world, rank, local):
             "padded_keys_per_s": world * padded * args.steps / (ms * 1e-3),
             "divergent": {"value": world * real * args.steps / (out["divergent"] * 1e-3),
                           "ms_per_step": out["divergent"] / args.steps},
+            "autotuned": {"value": world * real * args.steps / (out["auto"] * 1e-3),
+                          "ms_per_step": out["auto"] / args.steps, "tuning": tuned},
             "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)

@@ -168,7 +168,26 @@ int darm_segmented_sort_noalloc(uint32_t* keys, uint32_t* vals, const uint64_t* 
  * synchronises the device. */
 int darm_autotune(int dtype, size_t n, int has_vals, const char* db_path);
 
-/* Load plans previously written by darm_autotune. */
+/* Autotuner for batched segmented sorts (darm_segmented_sort with DARM_AUTO,
+ * and darm_segmented_sort_noalloc).  The paper treats the block size as a
+ * tunable evaluated per size (Section VI-A, "Block Size"); here every
+ * candidate tuning - tile size, register windows per window pass, elements
+ * per thread in window passes - is timed on whole batched sorts of the
+ * caller's own layout (keys/vals: DEVICE buffers laid out as for
+ * darm_segmented_sort; seg_offsets/seg_len: HOST arrays), then the
+ * divergent or melded form per pass kind (tile, window, merge).  The
+ * fastest becomes the batch tuning and is appended to db_path as a line
+ * with log2 n = 0 (NULL: memory only).  The segments are sorted in place
+ * several times (ascending); on return they hold the ascending sort.
+ * Allocates and frees its tables; synchronises the device.
+ * Errors: DARM_ERR_INVALID_ARG (no segments, misaligned buffers, or no
+ * candidate could run), DARM_ERR_NOT_POW2 (a capacity is not a power of
+ * two), DARM_ERR_CUDA. */
+int darm_autotune_segmented(uint32_t* keys, uint32_t* vals, const uint64_t* seg_offsets,
+                            const uint32_t* seg_len, uint32_t num_segs, const char* db_path);
+
+/* Load plans previously written by darm_autotune and
+ * darm_autotune_segmented (lines with log2 n = 0 are batch tunings). */
 int darm_load_tune_db(const char* db_path);
 
 /* ---- introspection ----------------------------------------------------- */

@@ -60,6 +60,7 @@ _sig = {
     "darm_segmented_sort_noalloc": ([_vp, _vp, _vp, _vp, ctypes.c_uint32, _i32, _i32, _vp, _vp],
                                     _i32),
     "darm_autotune": ([_i32, _sz, _i32, ctypes.c_char_p], _i32),
+    "darm_autotune_segmented": ([_vp, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_char_p], _i32),
     "darm_load_tune_db": ([ctypes.c_char_p], _i32),
     "darm_plan_info": ([_i32, _sz, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                         ctypes.POINTER(_i32)], _i32),
@@ -264,6 +265,26 @@ def sort_profile(keys, vals=None, descending: bool = False, variant="melded", st
 def autotune(dtype: int, n: int, has_vals: bool, db_path: str | None = None) -> None:
     _check(lib.darm_autotune(int(dtype), int(n), int(bool(has_vals)),
                              None if db_path is None else db_path.encode()), "darm_autotune")
+
+
+def autotune_segmented(keys, vals, offsets, lengths, db_path: str | None = None) -> None:
+    """Tune batched segmented sorts on this layout (see segmented_sort for the
+    arguments); the segments are left sorted ascending.  Later
+    segmented_sort(..., variant="auto") calls use the result."""
+    import numpy as np
+    import torch
+    if keys.dtype != torch.uint32 or not keys.is_cuda or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous uint32 CUDA tensor")
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    ln = np.ascontiguousarray(lengths, dtype=np.uint32)
+    if off.size != ln.size + 1:
+        raise ValueError("offsets must have num_segments + 1 entries")
+    vp = None if vals is None else ctypes.c_void_p(vals.data_ptr())
+    rc = lib.darm_autotune_segmented(ctypes.c_void_p(keys.data_ptr()), vp,
+                                     off.ctypes.data_as(ctypes.c_void_p),
+                                     ln.ctypes.data_as(ctypes.c_void_p), ln.size,
+                                     None if db_path is None else db_path.encode())
+    _check(rc, "darm_autotune_segmented")
 
 
 def load_tune_db(db_path: str) -> None:

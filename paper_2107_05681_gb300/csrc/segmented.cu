@@ -95,12 +95,11 @@ int log2u(uint64_t v) {
 
 // Build the launch list, device tables and graph for one layout.
 int build_seg_plan(SegPlan& sp, uint32_t* keys, uint32_t* vals, const std::vector<BatchSeg>& segs,
-                   int variant) {
+                   int variant, const Tuning& tn) {
   const bool has_vals = vals != nullptr;
   const KeyKind kk = KEY_U32;
   int cmax = 0;
   for (const BatchSeg& s : segs) cmax = std::max(cmax, s.c);
-  const Tuning tn = batch_tuning(kk, has_vals, cmax);
   BatchTables bt;
   int rc = batch_append(bt, kk, has_vals, tn, variant, segs, 0, 0);
   for (int p = tn.t + 1; p <= cmax && rc == DARM_OK; ++p)
@@ -174,6 +173,14 @@ uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
   return h;
 }
 
+// Every field of a tuning that changes a batch's launches.
+uint64_t tuning_key(const Tuning& tn) {
+  uint64_t k = 0;
+  for (int v : {tn.t, tn.e1, tn.e2, tn.c2, tn.w2, tn.tma, tn.var[0], tn.var[1], tn.var[2]})
+    k = k * 64 + uint64_t(v & 63);
+  return k;
+}
+
 }  // namespace
 
 int segmented_parse(const uint64_t* seg_offsets, const uint32_t* seg_len, uint32_t num_segs, int dir,
@@ -225,12 +232,15 @@ extern "C" int darm_segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_
   if (prc != DARM_OK) return prc;
   if (segs.empty()) return DARM_OK;
 
-  // layout key: pointers, direction, variant and a hash of the arrays
+  // layout key: pointers, direction, variant, the tuning the batch runs with
+  // and a hash of the arrays
   uint64_t h = 0xCBF29CE484222325ull;
   h = fnv1a(h, seg_offsets, sizeof(uint64_t) * (size_t(num_segs) + 1));
   h = fnv1a(h, seg_len, sizeof(uint32_t) * num_segs);
   if (seg_desc) h = fnv1a(h, seg_desc, num_segs);
-  const Tuning tn = tuning_for(KEY_U32, vals != nullptr, 0);
+  int cmax = 0;
+  for (const BatchSeg& sg : segs) cmax = std::max(cmax, sg.c);
+  const Tuning tn = batch_tuning(KEY_U32, vals != nullptr, cmax);
   std::vector<uint64_t> key = {h,
                                uint64_t(num_segs),
                                reinterpret_cast<uint64_t>(keys),
@@ -238,18 +248,119 @@ extern "C" int darm_segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_
                                uint64_t(dir),
                                uint64_t(variant),
                                uint64_t(seg_desc != nullptr),
-                               uint64_t(tn.t * 1000 + tn.e1 * 100 + tn.e2 * 10 + tn.w2)};
+                               tuning_key(tn)};
 
   std::lock_guard<std::mutex> lk(g_seg_mu);
   auto it = g_seg_plans.find(key);
   if (it == g_seg_plans.end()) {
     auto sp = std::make_unique<SegPlan>();
-    const int rc = build_seg_plan(*sp, keys, vals, segs, variant);
+    const int rc = build_seg_plan(*sp, keys, vals, segs, variant, tn);
     if (rc != DARM_OK) return rc;
     it = g_seg_plans.emplace(key, std::move(sp)).first;
   }
   SegPlan& sp = *it->second;
   if (cudaGraphLaunch(sp.exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) return DARM_ERR_CUDA;
   g_ctx.launches.fetch_add(uint64_t(sp.kernel_nodes), std::memory_order_relaxed);
+  return DARM_OK;
+}
+
+// Autotuner for batches: times whole batched sorts of the caller's layout for
+// each candidate tuning (tile size, register windows per window pass,
+// elements per thread in window passes), then the divergent or melded form
+// per pass kind, and keeps the fastest as the batch tuning.
+extern "C" int darm_autotune_segmented(uint32_t* keys, uint32_t* vals, const uint64_t* seg_offsets,
+                                       const uint32_t* seg_len, uint32_t num_segs,
+                                       const char* db_path) {
+  if (!g_ctx.inited) return DARM_ERR_NOT_INIT;
+  if (!keys || !seg_offsets || !seg_len || num_segs == 0) return DARM_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(keys) & 15u) != 0) return DARM_ERR_INVALID_ARG;
+  if (vals && (reinterpret_cast<uintptr_t>(vals) & 15u) != 0) return DARM_ERR_INVALID_ARG;
+  std::vector<BatchSeg> segs;
+  int rc = segmented_parse(seg_offsets, seg_len, num_segs, DARM_ASC, nullptr, segs);
+  if (rc != DARM_OK) return rc;
+  if (segs.empty()) return DARM_ERR_INVALID_ARG;
+  const bool hv = vals != nullptr;
+  int cmax = 0;
+  for (const BatchSeg& sg : segs) cmax = std::max(cmax, sg.c);
+
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return DARM_ERR_CUDA;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  // best of three replays of the batch's graph (after one warm-up); < 0 if
+  // the tuning cannot run this layout
+  auto time_tuning = [&](const Tuning& tn0) -> float {
+    Tuning tn = tn0;
+    tn.tma = 0;
+    if (!fit_tuning(tn, KEY_U32, hv, std::max(cmax, tn.t), g_ctx.smem_limit)) return -1.f;
+    SegPlan sp;
+    if (build_seg_plan(sp, keys, vals, segs, DARM_AUTO, tn) != DARM_OK) {
+      cudaGetLastError();
+      return -1.f;
+    }
+    float best = -1.f;
+    for (int r = 0; r < 4; ++r) {
+      cudaEventRecord(e0, s);
+      if (cudaGraphLaunch(sp.exec, s) != cudaSuccess) return -1.f;
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0 && (best < 0.f || ms < best)) best = ms;
+    }
+    return best;
+  };
+
+  const Tuning base = default_tuning(KEY_U32, hv);
+  Tuning best = base;
+  float best_ms = -1.f;
+  for (int t = base.t - 1; t <= base.t + 1; ++t)
+    for (int e2 = 3; e2 <= 5; ++e2)
+      for (int w2 = 1; w2 <= 2; ++w2) {
+        Tuning tn = base;
+        tn.t = t;
+        tn.e2 = e2;
+        tn.w2 = w2;
+        tn.tma = 0;
+        tn.var[0] = tn.var[1] = tn.var[2] = kMelded;
+        const float ms = time_tuning(tn);
+        if (ms >= 0.f && (best_ms < 0.f || ms < best_ms)) {
+          best_ms = ms;
+          best = tn;
+        }
+      }
+  // the divergent or melded form per pass kind (tile, window, merge)
+  if (best_ms >= 0.f) {
+    const Tuning shape = best;
+    for (int combo = 0; combo < 8; ++combo) {
+      Tuning tn = shape;
+      for (int k = 0; k < 3; ++k) tn.var[k] = ((combo >> k) & 1) ? kDivergent : kMelded;
+      if (combo == 0) continue;  // all melded: timed above
+      const float ms = time_tuning(tn);
+      if (ms >= 0.f && ms < best_ms) {
+        best_ms = ms;
+        best = tn;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  if (cudaGetLastError() != cudaSuccess) return DARM_ERR_CUDA;
+  if (best_ms < 0.f) return DARM_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lk(g_ctx.mu);
+    g_ctx.tuned[std::make_tuple(int(KEY_U32), int(hv), 0)] = best;
+  }
+  segmented_release_all();  // graphs built under the previous tuning
+  if (db_path) {
+    FILE* f = fopen(db_path, "a");
+    if (!f) return DARM_ERR_INVALID_ARG;
+    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %.6f\n", int(KEY_U32), int(hv), 0, best.t,
+            best.e1, best.e2, best.c2, best.w2, best.tma, best.var[0], best.var[1], best.var[2],
+            double(best_ms));
+    fclose(f);
+  }
   return DARM_OK;
 }

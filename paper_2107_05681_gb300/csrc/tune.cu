@@ -132,7 +132,6 @@ int darm_autotune(int dtype, size_t n, int has_vals, const char* db_path) {
   {
     std::lock_guard<std::mutex> lk(g_ctx.mu);
     g_ctx.tuned[std::make_tuple(int(kk), int(hv), m)] = best;
-    if (n <= (size_t(1) << 16)) g_ctx.tuned[std::make_tuple(int(kk), int(hv), 0)] = best;
     g_ctx.plans.clear();
   }
   cudaStreamDestroy(s);
@@ -163,12 +162,11 @@ int darm_load_tune_db(const char* db_path) {
   while (fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %lf", &kk, &hv, &m, &tn.t, &tn.e1,
                 &tn.e2, &tn.c2, &tn.w2, &tn.tma, &tn.var[0], &tn.var[1], &tn.var[2], &ms) == 13) {
     if (kk < 0 || kk > 1 || m < 0 || m > 31) continue;
-    g_ctx.tuned[std::make_tuple(kk, hv, m)] = tn;
-    if (m <= 16) g_ctx.tuned[std::make_tuple(kk, hv, 0)] = tn;
+    g_ctx.tuned[std::make_tuple(kk, hv, m)] = tn;  // m == 0: a batch tuning
     ++loaded;
   }
   fclose(f);
-  g_ctx.plans.clear();
+  g_ctx.plans.clear();  // batch graphs are keyed by their tuning
   return loaded ? DARM_OK : DARM_ERR_NOT_FOUND;
 }
 

@@ -133,3 +133,22 @@ def test_cfg4_full_10000_segments(darm, variant):
     assert_equal("keys", gk, ek)
     assert_equal("payload", gv, ev)
     assert darm.device_status() == darm.OK
+
+
+def test_autotune_segmented_then_auto(darm, tmp_path):
+    """The batch autotuner times whole batched sorts of the layout, leaves the
+    segments sorted, persists its choice (a log2 n = 0 line) and later
+    DARM_AUTO batched sorts with the tuned plan stay bit-exact."""
+    segs = synth.cfg4_segments(seed=77, num_segments=300, largest_first=True)
+    db = str(tmp_path / "seg.db")
+    k, v = to_dev(segs.keys), to_dev(segs.vals)
+    darm.autotune_segmented(k, v, segs.offsets, segs.lengths, db)
+    ek, ev = _expect(segs)
+    assert_equal("keys after tuning", k.cpu().numpy(), ek)
+    lines = [ln.split() for ln in open(db).read().split("\n") if ln.strip()]
+    assert len(lines) == 1 and lines[0][2] == "0"
+    darm.load_tune_db(db)
+    k, v = to_dev(segs.keys), to_dev(segs.vals)
+    darm.segmented_sort(k, v, segs.offsets, segs.lengths, variant="auto")
+    assert_equal("keys", k.cpu().numpy(), ek)
+    assert_equal("payload", v.cpu().numpy(), ev)
