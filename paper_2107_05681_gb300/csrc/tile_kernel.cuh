@@ -137,10 +137,26 @@ struct Interleave {
 __host__ __device__ constexpr uint32_t phys8_c(uint32_t l) { return l + ((l >> 4) << 1); }
 __host__ __device__ constexpr uint32_t phys_c(uint32_t l) { return l + ((l >> 5) << 2); }
 
+// Pad words per 32 elements of the tile kernels' own shared memory.  Tiles
+// of 32-bit keys without payload and 32 keys per thread pad one word per 32
+// keys: local bit b >= 5 then moves an index by 2^(b-5) banks, so the lanes
+// of every round (local bits 0..a-1 and a+5..9 for a window at bit a) fall
+// on 32 distinct banks, including the rounds whose window starts at bits
+// 1..4, where four pad words per 32 keys leave 2- to 4-way conflicts.  The
+// price is that the bottom-window rounds (window at bit 0) move words one at
+// a time instead of in 16-byte vectors (same wavefronts, more instructions).
+// Other shapes keep four pad words (16-byte aligned rows).
+template <typename K, bool V, int LOGE>
+struct TilePad {
+  static constexpr int value = (!V && sizeof(K) == 4 && LOGE == 5) ? 1 : 4;
+};
+template <int PAD>
+__host__ __device__ constexpr uint32_t physp(uint32_t l) { return l + (l >> 5) * uint32_t(PAD); }
+
 // Static-offset element access: register r of a round with window A sits at
 // local index tl | (r << A); phys() is additive over disjoint bits, so its
 // shared-memory word is phys(tl) + phys(r << A), a compile-time offset.
-template <typename K, bool V, int LOGE, int A, bool REV>
+template <typename K, bool V, int LOGE, int A, bool REV, int PAD = 4>
 __device__ __forceinline__ void s_load(K (&kr)[1 << LOGE], uint32_t (&vr)[1 << LOGE], bool from_global,
                                        const K* __restrict__ gk, const uint32_t* __restrict__ gv,
                                        uint32_t g_t, const K* sk, const uint32_t* sv,
@@ -201,7 +217,7 @@ __device__ __forceinline__ void s_load(K (&kr)[1 << LOGE], uint32_t (&vr)[1 << L
       }
     }
   } else {
-    if constexpr (A == 0 && E >= KPV) {
+    if constexpr (PAD == 4 && A == 0 && E >= KPV) {
 #pragma unroll
       for (int q0 = 0; q0 < E / KPV; ++q0) {
         const int q = REV ? (E / KPV - 1 - q0) : q0;
@@ -228,7 +244,7 @@ __device__ __forceinline__ void s_load(K (&kr)[1 << LOGE], uint32_t (&vr)[1 << L
 #pragma unroll
       for (int r0 = 0; r0 < E; ++r0) {
         const int r = REV ? (E - 1 - r0) : r0;
-        const uint32_t off = uint32_t(r << A) + ((uint32_t(r << A) >> 5) << 2);
+        const uint32_t off = physp<PAD>(uint32_t(r << A));
         kr[r] = sk[s_base + off] ^ m;
         if (V) vr[r] = sv[s_base + off];
       }
@@ -236,7 +252,7 @@ __device__ __forceinline__ void s_load(K (&kr)[1 << LOGE], uint32_t (&vr)[1 << L
   }
 }
 
-template <typename K, bool V, int LOGE, int A, bool REV, bool WIDE = false>
+template <typename K, bool V, int LOGE, int A, bool REV, bool WIDE = false, int PAD = 4>
 __device__ __forceinline__ void s_store(const K (&kr)[1 << LOGE], const uint32_t (&vr)[1 << LOGE],
                                         bool to_global, K* __restrict__ gk, uint32_t* __restrict__ gv,
                                         uint32_t g_t, K* sk, uint32_t* sv, uint32_t s_base,
@@ -316,7 +332,7 @@ __device__ __forceinline__ void s_store(const K (&kr)[1 << LOGE], const uint32_t
       }
     }
   } else {
-    if constexpr (A == 0 && E >= KPV) {
+    if constexpr (PAD == 4 && A == 0 && E >= KPV) {
 #pragma unroll
       for (int q0 = 0; q0 < E / KPV; ++q0) {
         const int q = REV ? (E / KPV - 1 - q0) : q0;
@@ -345,7 +361,7 @@ __device__ __forceinline__ void s_store(const K (&kr)[1 << LOGE], const uint32_t
 #pragma unroll
       for (int r0 = 0; r0 < E; ++r0) {
         const int r = REV ? (E - 1 - r0) : r0;
-        const uint32_t off = uint32_t(r << A) + ((uint32_t(r << A) >> 5) << 2);
+        const uint32_t off = physp<PAD>(uint32_t(r << A));
         sk[s_base + off] = kr[r] ^ m;
         if (V) sv[s_base + off] = vr[r];
       }
@@ -358,6 +374,7 @@ __device__ __forceinline__ void s_store(const K (&kr)[1 << LOGE], const uint32_t
 template <typename K, bool V, int LOGE, int LOGT, int VAR, bool MERGE>
 __device__ __forceinline__ void tile_block(const PassParams& P, uint32_t bidx, K* sk, uint32_t* sv) {
   constexpr int E = 1 << LOGE;
+  constexpr int PADT = TilePad<K, V, LOGE>::value;
   K* __restrict__ gk = reinterpret_cast<K*>(P.keys);
   uint32_t* __restrict__ gv = P.vals;
   const uint32_t tid = threadIdx.x;
@@ -400,7 +417,7 @@ __device__ __forceinline__ void tile_block(const PassParams& P, uint32_t bidx, K
     const bool to_global = last || (R.dst == LOC_GLOBAL);
     const uint32_t tl = (tid & ((1u << A) - 1u)) | ((tid >> A) << (A + LOGE));
     const uint32_t g_full = tl | gblk;
-    const uint32_t s_base = Interleave<K, V>::value ? phys8(tl) : phys(tl);
+    const uint32_t s_base = Interleave<K, V>::value ? phys8(tl) : physp<PADT>(tl);
     uint32_t min_ = 0, mout = 0, g_t = g_full;
     K* bk = gk;
     uint32_t* bv = gv;
@@ -424,7 +441,7 @@ __device__ __forceinline__ void tile_block(const PassParams& P, uint32_t bidx, K
     const bool do_store = !(to_global && skip);
 
     if constexpr (R.kind == RK_PHASE_A) {
-      if (!skip) s_load<K, V, LOGE, 0, false>(kr, vr, true, bk, bv, g_t, sk, sv, s_base, min_, K(0));
+      if (!skip) s_load<K, V, LOGE, 0, false, PADT>(kr, vr, true, bk, bv, g_t, sk, sv, s_base, min_, K(0));
       if (fill) {
         bool collide = false;
 #pragma unroll
@@ -458,30 +475,30 @@ __device__ __forceinline__ void tile_block(const PassParams& P, uint32_t bidx, K
         }
       }
       if (do_store)
-        s_store<K, V, LOGE, 0, false>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, K(0));
+        s_store<K, V, LOGE, 0, false, false, PADT>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, K(0));
     } else {
       const uint32_t p = MERGE ? merge_p : uint32_t(R.p);
       const bool asc = ((g_dir & (1u << p) & capmask) == 0u);
       if (VAR == kDivergent || !R.lanediv) {
         // Fig. 1: one full copy of the body per direction
         if (asc) {
-          s_load<K, V, LOGE, A, false>(kr, vr, from_global, bk, bv, g_t, sk, sv, s_base, min_, K(0));
+          s_load<K, V, LOGE, A, false, PADT>(kr, vr, from_global, bk, bv, g_t, sk, sv, s_base, min_, K(0));
           window_side<K, V, LOGE, true>(kr, vr, R.cnt);
           if (do_store)
-            s_store<K, V, LOGE, A, false>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, K(0));
+            s_store<K, V, LOGE, A, false, false, PADT>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, K(0));
         } else {
-          s_load<K, V, LOGE, A, true>(kr, vr, from_global, bk, bv, g_t, sk, sv, s_base, min_, K(0));
+          s_load<K, V, LOGE, A, true, PADT>(kr, vr, from_global, bk, bv, g_t, sk, sv, s_base, min_, K(0));
           window_side<K, V, LOGE, false>(kr, vr, R.cnt);
           if (do_store)
-            s_store<K, V, LOGE, A, true>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, K(0));
+            s_store<K, V, LOGE, A, true, false, PADT>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, K(0));
         }
       } else {
         // melded: one copy; the descending side's keys enter complemented
         const K m = asc ? K(0) : ~K(0);
-        s_load<K, V, LOGE, A, false>(kr, vr, from_global, bk, bv, g_t, sk, sv, s_base, min_, m);
+        s_load<K, V, LOGE, A, false, PADT>(kr, vr, from_global, bk, bv, g_t, sk, sv, s_base, min_, m);
         window_side<K, V, LOGE, true>(kr, vr, R.cnt);
         if (do_store)
-          s_store<K, V, LOGE, A, false>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, m);
+          s_store<K, V, LOGE, A, false, false, PADT>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base, mout, m);
       }
     }
     if (to_global) {
