@@ -22,6 +22,7 @@ template <typename K, bool V, int LOGE, int C, int VAR, int MAXT>
 __global__ void __launch_bounds__(MAXT, (MAXT >= 1024) ? 1 : 1024 / MAXT) darm_window2_kernel(const __grid_constant__ PassParams P) {
   constexpr int E = 1 << LOGE;
   constexpr int B = C + 2 * LOGE;  // log2 block elements
+  constexpr int PAD = TilePad<K, V, LOGE>::value;  // pad words per 32 elements
   constexpr uint32_t SW = smem_words(1u << B);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   K* sk = reinterpret_cast<K*>(smem_raw);
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT >= 1024) ? 1 : 1024 / MAXT) darm_w
     const uint32_t tl = (tid & ((1u << A) - 1u)) | ((tid >> A) << (A + LOGE));
     const uint32_t g_t = (tl & ((1u << C) - 1u)) | ((tl >> C) << w0) | gblk;
     const uint32_t sh = w0 + uint32_t(LOGE);  // register r sits at g_t + (r << sh)
-    const uint32_t s_base = Interleave<K, V>::value ? phys8(tl) : phys(tl);
+    const uint32_t s_base = Interleave<K, V>::value ? phys8(tl) : physp<PAD>(tl);
     auto body = [&](auto asc_c) {
       constexpr bool ASC = decltype(asc_c)::value;
 #pragma unroll
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT >= 1024) ? 1 : 1024 / MAXT) darm_w
         if (V) vr[r] = gv[g];
       }
       window_side<K, V, LOGE, ASC>(kr, vr, LOGE);
-      s_store<K, V, LOGE, A, false>(kr, vr, false, gk, gv, 0u, sk, sv, s_base, 0u, K(0));
+      s_store<K, V, LOGE, A, false, false, PAD>(kr, vr, false, gk, gv, 0u, sk, sv, s_base, 0u, K(0));
     };
     if (asc)
       body(std::true_type{});
@@ -74,10 +75,10 @@ __global__ void __launch_bounds__(MAXT, (MAXT >= 1024) ? 1 : 1024 / MAXT) darm_w
     constexpr int A = C;
     const uint32_t tl = (tid & ((1u << A) - 1u)) | ((tid >> A) << (A + LOGE));
     const uint32_t g_t = (tl & ((1u << C) - 1u)) | ((tl >> C) << w0) | gblk;
-    const uint32_t s_base = Interleave<K, V>::value ? phys8(tl) : phys(tl);
+    const uint32_t s_base = Interleave<K, V>::value ? phys8(tl) : physp<PAD>(tl);
     auto body = [&](auto asc_c) {
       constexpr bool ASC = decltype(asc_c)::value;
-      s_load<K, V, LOGE, A, false>(kr, vr, false, gk, gv, 0u, sk, sv, s_base, 0u, K(0));
+      s_load<K, V, LOGE, A, false, PAD>(kr, vr, false, gk, gv, 0u, sk, sv, s_base, 0u, K(0));
       window_side<K, V, LOGE, ASC>(kr, vr, cnt1);
 #pragma unroll
       for (int r = 0; r < E; ++r) {
