@@ -161,6 +161,10 @@ int darm_sort_init(int device, size_t workspace_bytes) {
   if (cudaMemset(g_ctx.d_status, 0, sizeof(int)) != cudaSuccess) return DARM_ERR_CUDA;
   if (cudaStreamCreateWithFlags(&g_ctx.host_stream, cudaStreamNonBlocking) != cudaSuccess)
     return DARM_ERR_CUDA;
+  if (cudaStreamCreateWithFlags(&g_ctx.host_copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return DARM_ERR_CUDA;
+  for (cudaEvent_t& e : g_ctx.host_chunk_ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return DARM_ERR_CUDA;
   if (workspace_bytes) {
     if (cudaMalloc(&g_ctx.ws, workspace_bytes) != cudaSuccess) return DARM_ERR_OOM;
     g_ctx.ws_bytes = workspace_bytes;
@@ -180,6 +184,12 @@ int darm_sort_finalize(void) {
   if (g_ctx.ws) cudaFree(g_ctx.ws);
   if (g_ctx.d_status) cudaFree(g_ctx.d_status);
   if (g_ctx.host_stream) cudaStreamDestroy(g_ctx.host_stream);
+  if (g_ctx.host_copy_stream) cudaStreamDestroy(g_ctx.host_copy_stream);
+  for (cudaEvent_t& e : g_ctx.host_chunk_ev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
+  g_ctx.host_copy_stream = nullptr;
   g_ctx.ws = nullptr;
   g_ctx.ws_bytes = 0;
   g_ctx.d_status = nullptr;
@@ -236,6 +246,107 @@ int darm_bitonic_sort_u64(uint64_t* keys, uint32_t* vals, size_t n, int dir, int
                      static_cast<cudaStream_t>(stream));
 }
 
+}  // extern "C"
+
+namespace darm {
+namespace {
+
+// Host-buffer sorts of 2^m >= 2^kHostChunkMinLog2 elements overlap the
+// host->device copy with the tile pass.  The tile pass compares elements of
+// one tile only, so the input is copied in 8 chunks on a copy stream and the
+// tile pass of each chunk (its directions read from the chunk's index in the
+// whole array: dir_base) runs as soon as the chunk has arrived, while the
+// next chunk is still being copied; the window and merge passes then run
+// over the whole array.  Every comparator is the whole-array network's, so
+// the result is identical.  (Running more stages per chunk turns every
+// window and merge pass into a launch too small to fill the GPU, which cost
+// more than the copy it hid.)
+constexpr int kHostChunkMinLog2 = 20;
+constexpr int kHostChunks = 8;
+
+int sort_host_chunked(KeyKind kk, bool f32, void* keys_out, uint32_t* vals_out, void* dk,
+                      uint32_t* dv, int m, int dir, int variant, cudaStream_t s) {
+  const void* keys = keys_out;
+  const uint32_t* vals = vals_out;
+  const int mc = m - 3;
+  const size_t cn = size_t(1) << mc;
+  const size_t ksz = (kk == KEY_U64) ? 8 : 4;
+  const bool hv = vals != nullptr;
+  const uint32_t map = (f32 ? kMapF32 : 0u) | (dir == DARM_DESC ? kMapComplement : 0u);
+  const std::vector<Launch>* full = cached_plan(kk, hv, m, variant, map, map);
+  if (!full || full->empty() || full->front().kind != PASS_TILE) return DARM_ERR_INVALID_ARG;
+  std::vector<Launch> tile(1, full->front());
+  const int t = int(tile[0].P.b);
+  if (mc < t || tile[0].P.work_counter != nullptr) return DARM_ERR_INVALID_ARG;
+  tile[0].grid = uint32_t(1u << (mc - t));
+  // The final stage's trailing passes whose blocks lie inside one chunk (the
+  // merge, and window passes whose window stays below bit mc) also run chunk
+  // by chunk at the end, so that each chunk's device->host copy overlaps the
+  // next chunk's passes.
+  size_t tail_begin = full->size();
+  while (tail_begin > 1) {
+    const Launch& L = (*full)[tail_begin - 1];
+    if (int(L.P.rounds[0].p) != m || L.P.work_counter != nullptr) break;
+    const bool local = (L.kind == PASS_MERGE) ||
+                       (L.kind == PASS_WINDOW && int(L.P.w0 + L.P.s) <= mc && int(L.P.b) <= mc);
+    if (!local) break;
+    --tail_begin;
+  }
+  const std::vector<Launch> body(full->begin() + 1, full->begin() + tail_begin);
+  std::vector<Launch> tail(full->begin() + tail_begin, full->end());
+  for (Launch& L : tail) {
+    if (L.tma) {
+      L.P.nblocks = uint32_t(1u << (mc - int(L.P.b)));
+      L.grid = std::min(L.grid, L.P.nblocks);
+    } else {
+      L.grid >>= 3;  // 2^(m - b) blocks -> 2^(mc - b) per chunk
+    }
+  }
+  cudaStream_t cps = g_ctx.host_copy_stream;
+  for (int c = 0; c < kHostChunks; ++c) {
+    const size_t off = size_t(c) * cn;
+    char* kdst = static_cast<char*>(dk) + off * ksz;
+    const char* ksrc = static_cast<const char*>(keys) + off * ksz;
+    if (cudaMemcpyAsync(kdst, ksrc, cn * ksz, cudaMemcpyHostToDevice, cps) != cudaSuccess)
+      return DARM_ERR_CUDA;
+    if (hv && cudaMemcpyAsync(dv + off, vals + off, cn * 4, cudaMemcpyHostToDevice, cps) !=
+                  cudaSuccess)
+      return DARM_ERR_CUDA;
+    if (cudaEventRecord(g_ctx.host_chunk_ev[c], cps) != cudaSuccess) return DARM_ERR_CUDA;
+    if (cudaStreamWaitEvent(s, g_ctx.host_chunk_ev[c], 0) != cudaSuccess) return DARM_ERR_CUDA;
+    tile[0].P.dir_base = uint32_t(off);
+    const int rc = launch_plan(tile, kk, kdst, hv ? dv + off : nullptr, s);
+    if (rc != DARM_OK) return rc;
+  }
+  int rc = launch_plan(body, kk, dk, dv, s);
+  if (rc != DARM_OK) return rc;
+  for (int c = 0; c < kHostChunks; ++c) {
+    const size_t off = size_t(c) * cn;
+    char* kd = static_cast<char*>(dk) + off * ksz;
+    if (!tail.empty()) {
+      rc = launch_plan(tail, kk, kd, hv ? dv + off : nullptr, s);
+      if (rc != DARM_OK) return rc;
+    }
+    if (cudaEventRecord(g_ctx.host_chunk_ev[c], s) != cudaSuccess) return DARM_ERR_CUDA;
+    if (cudaStreamWaitEvent(cps, g_ctx.host_chunk_ev[c], 0) != cudaSuccess) return DARM_ERR_CUDA;
+    if (cudaMemcpyAsync(static_cast<char*>(keys_out) + off * ksz, kd, cn * ksz,
+                        cudaMemcpyDeviceToHost, cps) != cudaSuccess)
+      return DARM_ERR_CUDA;
+    if (hv && cudaMemcpyAsync(vals_out + off, dv + off, cn * 4, cudaMemcpyDeviceToHost, cps) !=
+                  cudaSuccess)
+      return DARM_ERR_CUDA;
+  }
+  // the caller synchronises `s`: make it wait for the last copies
+  if (cudaEventRecord(g_ctx.host_chunk_ev[0], cps) != cudaSuccess) return DARM_ERR_CUDA;
+  if (cudaStreamWaitEvent(s, g_ctx.host_chunk_ev[0], 0) != cudaSuccess) return DARM_ERR_CUDA;
+  return DARM_OK;
+}
+
+}  // namespace
+}  // namespace darm
+
+extern "C" {
+
 int darm_bitonic_sort_host(void* keys, uint32_t* vals, size_t n, int dtype, int dir,
                            int variant) {
   if (!g_ctx.inited) return DARM_ERR_NOT_INIT;
@@ -258,14 +369,20 @@ int darm_bitonic_sort_host(void* keys, uint32_t* vals, size_t n, int dtype, int 
   void* dk = base;
   uint32_t* dv = vals ? reinterpret_cast<uint32_t*>(base + ((kbytes + 255) & ~size_t(255))) : nullptr;
   cudaStream_t s = g_ctx.host_stream;
-  if (cudaMemcpyAsync(dk, keys, kbytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return DARM_ERR_CUDA;
+  const KeyKind kk = dtype == DARM_U64 ? KEY_U64 : KEY_U32;
+  const int m = log2_exact(n);
+  if (m >= kHostChunkMinLog2) {
+    // copies in both directions happen inside, overlapped with passes
+    const int rc = sort_host_chunked(kk, dtype == DARM_F32, keys, vals, dk, dv, m, dir, variant, s);
+    if (rc != DARM_OK) return rc;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return DARM_ERR_CUDA;
+    return DARM_OK;
+  }
+  if (cudaMemcpyAsync(dk, keys, kbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return DARM_ERR_CUDA;
   if (vals && cudaMemcpyAsync(dv, vals, vbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return DARM_ERR_CUDA;
-  int rc;
-  if (dtype == DARM_U64)
-    rc = sort_device(KEY_U64, false, dk, dv, n, dir, variant, s);
-  else
-    rc = sort_device(KEY_U32, dtype == DARM_F32, dk, dv, n, dir, variant, s);
+  const int rc = sort_device(kk, dtype == DARM_F32, dk, dv, n, dir, variant, s);
   if (rc != DARM_OK) return rc;
   if (cudaMemcpyAsync(keys, dk, kbytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DARM_ERR_CUDA;
   if (vals && cudaMemcpyAsync(vals, dv, vbytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)

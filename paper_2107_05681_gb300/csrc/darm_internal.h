@@ -25,6 +25,8 @@ struct Context {
   size_t smem_limit = 0;
   int* d_status = nullptr;           // device status word
   cudaStream_t host_stream = nullptr;  // stream of host-buffer sorts
+  cudaStream_t host_copy_stream = nullptr;  // their chunked host->device copies
+  cudaEvent_t host_chunk_ev[8] = {};        // one per chunk copied
   void* ws = nullptr;                // workspace of host-buffer sorts
   size_t ws_bytes = 0;
   std::mutex mu;       // plans, tuning table, init/finalize

@@ -112,7 +112,10 @@ struct PassParams {
   int* status;             // device status word (sentinel collisions)
   unsigned int* work_counter;  // persistent launches: next block to take
   uint32_t nblocks;            // persistent launches: blocks in the table
-  uint32_t pad2;
+  uint32_t dir_base;           // single arrays: index of element 0 in the array
+                               // whose network sets the directions (a chunk
+                               // sorted on its own through its first stages:
+                               // its offset); 0 otherwise
   Round rounds[kMaxRounds];
 };
 
@@ -611,8 +614,9 @@ __global__ void __launch_bounds__(MAXT, 1) darm_pass_kernel(const __grid_constan
     }
     const uint8_t src_e = (skip_mem && src == LOC_GLOBAL) ? uint8_t(LOC_NONE) : src;
     const uint8_t dst_e = (skip_mem && dst == LOC_GLOBAL) ? uint8_t(LOC_NONE) : dst;
-    // direction bits are read from the index within the segment
-    const uint32_t g_dir = g_full & capmask;
+    // direction bits are read from the index within the segment (or, for a
+    // chunk of a larger array, within that array)
+    const uint32_t g_dir = (g_full | P.dir_base) & capmask;
     // the planner marks rounds whose direction can differ between the
     // lanes of a warp; only those are melded
     const bool lane_divergent = R.lanediv != 0;

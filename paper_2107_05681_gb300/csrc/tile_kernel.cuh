@@ -437,7 +437,7 @@ __device__ __forceinline__ void tile_block(const PassParams& P, uint32_t bidx, K
       if (rd == 0 && from_global) min_ = P.map_in;
       if (last) mout = P.map_out;
     }
-    const uint32_t g_dir = g_full & capmask;
+    const uint32_t g_dir = (g_full | P.dir_base) & capmask;
     const bool do_store = !(to_global && skip);
 
     if constexpr (R.kind == RK_PHASE_A) {

@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_ke
     const K* stage_k = reinterpret_cast<const K*>(smem_raw + size_t(b) * L::kStage);
     const uint32_t* stage_v = reinterpret_cast<const uint32_t*>(smem_raw + size_t(b) * L::kStage + L::kStageK);
     const uint32_t gblk = tile << LOGT;
-    const bool asc = ((gblk & (1u << p) & capmask) == 0u);
+    const bool asc = (((gblk | P.dir_base) & (1u << p) & capmask) == 0u);
     const uint32_t next = tile + uint32_t(NS) * gridDim.x;
 
     static_for<0, NR>([&](auto I) {

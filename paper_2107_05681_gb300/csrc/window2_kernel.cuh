@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT >= 1024) ? 1 : 1024 / MAXT) darm_w
   const uint32_t capmask = (1u << P.log2cap) - 1u;
   const uint32_t p = P.rounds[0].p;
   const int cnt1 = P.rounds[1].cnt;
-  const bool asc = ((gblk & (1u << p) & capmask) == 0u);
+  const bool asc = (((gblk | P.dir_base) & (1u << p) & capmask) == 0u);
 
   K kr[E];
   uint32_t vr[E];

@@ -173,6 +173,29 @@ def test_host_buffer_sort(darm):
     assert_equal("payload", v, ev)
 
 
+@pytest.mark.parametrize("case", ["kv_asc", "kv_desc", "f32_desc", "u64_kv", "kv_22"])
+def test_host_sort_chunked_overlap(darm, case):
+    """Host buffers of 2^20 or more elements are copied in 8 chunks whose
+    first stages run while later chunks are still being copied; the result
+    must equal the whole-array network's, payload order included."""
+    m = 22 if case == "kv_22" else 20
+    n = 1 << m
+    desc = case.endswith("desc")
+    if case == "f32_desc":
+        keys = synth.cfg3_f32(4100, n, dup_frac=0.02, zeros_each=64)
+    elif case == "u64_kv":
+        keys = synth.uniform_u64(4101, n) % np.uint64(1 << 40)
+    else:
+        keys = synth.uniform_u32(4102 + m, n) % np.uint32(n // 4)
+    vals = np.arange(n, dtype=np.uint32)
+    ek, ev = oracle.bitonic_sort(keys, vals, desc=desc)
+    k, v = keys.copy(), vals.copy()
+    darm.sort_host(k, v, descending=desc)
+    assert_equal("keys", k.view(np.uint32) if k.dtype == np.float32 else k,
+                 ek.view(np.uint32) if ek.dtype == np.float32 else ek)
+    assert_equal("payload", v, ev)
+
+
 def test_launch_counter_counts_kernels(darm):
     import torch
     before = darm.launch_count()
