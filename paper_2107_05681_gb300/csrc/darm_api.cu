@@ -252,15 +252,21 @@ namespace darm {
 namespace {
 
 // Host-buffer sorts of 2^m >= 2^kHostChunkMinLog2 elements overlap the
-// host->device copy with the tile pass.  The tile pass compares elements of
-// one tile only, so the input is copied in 8 chunks on a copy stream and the
-// tile pass of each chunk (its directions read from the chunk's index in the
-// whole array: dir_base) runs as soon as the chunk has arrived, while the
-// next chunk is still being copied; the window and merge passes then run
-// over the whole array.  Every comparator is the whole-array network's, so
-// the result is identical.  (Running more stages per chunk turns every
-// window and merge pass into a launch too small to fill the GPU, which cost
-// more than the copy it hid.)
+// host<->device copies with the sort.  A stage 2^p compares elements of one
+// aligned 2^p-element block only, so:
+//   - the input is copied in 8 chunks on a copy stream, and the tile pass of
+//     each chunk runs as soon as it has arrived;
+//   - once the first half (4 chunks) has arrived and been tiled, stages
+//     2^(t+1) .. 2^(m-1) run on that half while the second half is still
+//     being copied; then the second half's tile passes and stages;
+//   - the final stage runs over the whole array; its trailing passes whose
+//     blocks lie inside one chunk (the merge, and window passes below bit
+//     m-3) run chunk by chunk, and each chunk is copied back while the next
+//     one is processed.
+// A chunk or half reads its comparator directions from its index in the
+// whole array (dir_base), so every comparator is the whole-array network's
+// and the result is identical.  (Running all stages below 2^(m-3) per chunk
+// was slower: those launches are too small to fill the GPU.)
 constexpr int kHostChunkMinLog2 = 20;
 constexpr int kHostChunks = 8;
 
@@ -268,31 +274,45 @@ int sort_host_chunked(KeyKind kk, bool f32, void* keys_out, uint32_t* vals_out, 
                       uint32_t* dv, int m, int dir, int variant, cudaStream_t s) {
   const void* keys = keys_out;
   const uint32_t* vals = vals_out;
-  const int mc = m - 3;
-  const size_t cn = size_t(1) << mc;
+  const int mc = m - 3, mh = m - 1;
+  const size_t cn = size_t(1) << mc, hn = size_t(1) << mh;
   const size_t ksz = (kk == KEY_U64) ? 8 : 4;
   const bool hv = vals != nullptr;
   const uint32_t map = (f32 ? kMapF32 : 0u) | (dir == DARM_DESC ? kMapComplement : 0u);
   const std::vector<Launch>* full = cached_plan(kk, hv, m, variant, map, map);
   if (!full || full->empty() || full->front().kind != PASS_TILE) return DARM_ERR_INVALID_ARG;
+  // the half-size plan takes the whole array's tuning, so that its passes
+  // start where the whole array's tile pass ends
+  std::vector<Launch> hplan_v;
+  if (!plan_array(hplan_v, kk, hv, mh, tuning_for(kk, hv, m), variant, map, 0u, g_ctx.smem_limit))
+    return DARM_ERR_INVALID_ARG;
+  const std::vector<Launch>* hplan = &hplan_v;
+  if (hplan->empty() || hplan->front().kind != PASS_TILE ||
+      hplan->front().P.b != full->front().P.b)
+    return DARM_ERR_INVALID_ARG;
   std::vector<Launch> tile(1, full->front());
   const int t = int(tile[0].P.b);
   if (mc < t || tile[0].P.work_counter != nullptr) return DARM_ERR_INVALID_ARG;
   tile[0].grid = uint32_t(1u << (mc - t));
-  // The final stage's trailing passes whose blocks lie inside one chunk (the
-  // merge, and window passes whose window stays below bit mc) also run chunk
-  // by chunk at the end, so that each chunk's device->host copy overlaps the
-  // next chunk's passes.
+  // stages t+1 .. m-1 on one half: the half-size plan without its tile pass
+  std::vector<Launch> half(hplan->begin() + 1, hplan->end());
+  for (Launch& L : half) L.P.log2cap = uint32_t(m);  // directions of the whole array
+  // the final stage of the whole-array plan, split into a whole-array body
+  // and a chunk-local tail
+  size_t first = full->size();
+  while (first > 1 && (*full)[first - 1].kind != PASS_TILE &&
+         int((*full)[first - 1].P.rounds[0].p) == m)
+    --first;
   size_t tail_begin = full->size();
-  while (tail_begin > 1) {
+  while (tail_begin > first) {
     const Launch& L = (*full)[tail_begin - 1];
-    if (int(L.P.rounds[0].p) != m || L.P.work_counter != nullptr) break;
+    if (L.P.work_counter != nullptr) break;
     const bool local = (L.kind == PASS_MERGE) ||
                        (L.kind == PASS_WINDOW && int(L.P.w0 + L.P.s) <= mc && int(L.P.b) <= mc);
     if (!local) break;
     --tail_begin;
   }
-  const std::vector<Launch> body(full->begin() + 1, full->begin() + tail_begin);
+  const std::vector<Launch> body(full->begin() + first, full->begin() + tail_begin);
   std::vector<Launch> tail(full->begin() + tail_begin, full->end());
   for (Launch& L : tail) {
     if (L.tma) {
@@ -305,20 +325,30 @@ int sort_host_chunked(KeyKind kk, bool f32, void* keys_out, uint32_t* vals_out, 
   cudaStream_t cps = g_ctx.host_copy_stream;
   for (int c = 0; c < kHostChunks; ++c) {
     const size_t off = size_t(c) * cn;
-    char* kdst = static_cast<char*>(dk) + off * ksz;
-    const char* ksrc = static_cast<const char*>(keys) + off * ksz;
-    if (cudaMemcpyAsync(kdst, ksrc, cn * ksz, cudaMemcpyHostToDevice, cps) != cudaSuccess)
+    if (cudaMemcpyAsync(static_cast<char*>(dk) + off * ksz,
+                        static_cast<const char*>(keys) + off * ksz, cn * ksz,
+                        cudaMemcpyHostToDevice, cps) != cudaSuccess)
       return DARM_ERR_CUDA;
     if (hv && cudaMemcpyAsync(dv + off, vals + off, cn * 4, cudaMemcpyHostToDevice, cps) !=
                   cudaSuccess)
       return DARM_ERR_CUDA;
     if (cudaEventRecord(g_ctx.host_chunk_ev[c], cps) != cudaSuccess) return DARM_ERR_CUDA;
-    if (cudaStreamWaitEvent(s, g_ctx.host_chunk_ev[c], 0) != cudaSuccess) return DARM_ERR_CUDA;
-    tile[0].P.dir_base = uint32_t(off);
-    const int rc = launch_plan(tile, kk, kdst, hv ? dv + off : nullptr, s);
+  }
+  int rc;
+  for (int h = 0; h < 2; ++h) {
+    for (int c = h * kHostChunks / 2; c < (h + 1) * kHostChunks / 2; ++c) {
+      const size_t off = size_t(c) * cn;
+      if (cudaStreamWaitEvent(s, g_ctx.host_chunk_ev[c], 0) != cudaSuccess) return DARM_ERR_CUDA;
+      tile[0].P.dir_base = uint32_t(off);
+      rc = launch_plan(tile, kk, static_cast<char*>(dk) + off * ksz, hv ? dv + off : nullptr, s);
+      if (rc != DARM_OK) return rc;
+    }
+    const size_t off = size_t(h) * hn;
+    for (Launch& L : half) L.P.dir_base = uint32_t(off);
+    rc = launch_plan(half, kk, static_cast<char*>(dk) + off * ksz, hv ? dv + off : nullptr, s);
     if (rc != DARM_OK) return rc;
   }
-  int rc = launch_plan(body, kk, dk, dv, s);
+  rc = launch_plan(body, kk, dk, dv, s);
   if (rc != DARM_OK) return rc;
   for (int c = 0; c < kHostChunks; ++c) {
     const size_t off = size_t(c) * cn;
