@@ -97,27 +97,27 @@ int darm_autotune(int dtype, size_t n, int has_vals, const char* db_path) {
   float best_ms = 1e30f;
   const int t_cand[] = {base.t - 1, base.t, base.t + 1};
   const int e2_cand[] = {3, 4, 5};
-  for (int t : t_cand) {
-    for (int e2 : e2_cand) {
-      for (int w2 = 1; w2 <= 2; ++w2)
-      for (int tma = 0; tma <= 2; ++tma) {
-        Tuning tn = base;
-        tn.tma = tma;
-        tn.t = t;
-        tn.e2 = e2;
-        tn.w2 = w2;
-        tn.var[0] = tn.var[1] = tn.var[2] = kMelded;
-        std::vector<Launch> plan;
-        if (!plan_array(plan, kk, hv, m, tn, DARM_AUTO, 0, 0, g_ctx.smem_limit)) continue;
-        float kind[3], tot;
-        if (!time_plan(plan, kk, keys, vals, kbytes / 4, s, 3, kind, &tot)) continue;
-        if (tot < best_ms) {
-          best_ms = tot;
-          best = tn;
-        }
-      }
-    }
-  }
+  for (int t : t_cand)
+    for (int e1 = base.e1 - 1; e1 <= base.e1; ++e1)
+      for (int e2 : e2_cand)
+        for (int w2 = 1; w2 <= 2; ++w2)
+          for (int tma = 0; tma <= 2; ++tma) {
+            Tuning tn = base;
+            tn.tma = tma;
+            tn.t = t;
+            tn.e1 = e1;
+            tn.e2 = e2;
+            tn.w2 = w2;
+            tn.var[0] = tn.var[1] = tn.var[2] = kMelded;
+            std::vector<Launch> plan;
+            if (!plan_array(plan, kk, hv, m, tn, DARM_AUTO, 0, 0, g_ctx.smem_limit)) continue;
+            float kind[3], tot;
+            if (!time_plan(plan, kk, keys, vals, kbytes / 4, s, 3, kind, &tot)) continue;
+            if (tot < best_ms) {
+              best_ms = tot;
+              best = tn;
+            }
+          }
   // per pass kind: divergent or melded
   float kind_of[2][3];
   for (int v = 0; v < 2; ++v) {
