@@ -183,7 +183,7 @@ def run_reference(args, world, rank):
         "u32", "data": "synthetic",
         "config": {"workload": desc, "n": n_full},
         "cpu_baseline": {"value": value, "unit": "keys/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host": host_cpu()},
         "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -234,9 +234,36 @@ def cpu_baseline(keys, vals):
         dt += time.perf_counter() - t0
         reps += 1
     what = "one" if reps == 1 else f"{reps}"
+    # the textbook routine beside it: numpy's single-threaded sort of the same
+    # keys (keys only)
+    t0 = time.perf_counter()
+    lib_reps = 0
+    while time.perf_counter() - t0 < 0.5:
+        np.sort(keys[:n], kind="quicksort")
+        lib_reps += 1
+    lib_dt = time.perf_counter() - t0
     return {"value": reps * n / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
             "sample": f"{what} single-threaded oracle sort(s) of the first 2^{m} elements "
-                      f"({dt:.1f} s)"}
+                      f"({dt:.1f} s)",
+            "library_sort_keys_per_s": lib_reps * n / lib_dt,
+            "library_sort": "numpy.sort (introsort, one thread), keys only",
+            "host": host_cpu()}
+
+
+def host_cpu():
+    """Core count and CPU model of this host."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model", "hardware")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or
+            platform.machine()}
 
 
 def run_segmented(args, world, rank, local):
