@@ -63,7 +63,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
             print(res.stderr, flush=True)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, sources()))
     tmp = f"{LIB}.{os.getpid()}.tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]

@@ -1,42 +1,24 @@
-// tile_u32.cu - compile-time-schedule tile and merge kernels for uint32_t keys.
-#include "kernel_table.h"
-#include "tile_kernel.cuh"
+// tile_u32.cu - table of the compile-time-schedule tile and merge kernels for
+// uint32_t keys (instantiated in tile_u32_keys16.cu, tile_u32_keys32.cu and
+// tile_u32_pairs.cu) and the schedules the planner checks them against.
+#include "tile_entry.cuh"
 
 namespace darm {
 namespace {
-
-template <bool V, int LOGE, int LOGT, int VAR, bool MERGE>
-KernelEntry tentry() {
-  constexpr int MT = 1 << (LOGT - LOGE);  // one tile per CTA
-  static_assert((1 << (LOGT - LOGE)) <= MT, "tile too large for the block size");
-  return KernelEntry{
-      reinterpret_cast<const void*>(&darm_tile_kernel<uint32_t, V, LOGE, LOGT, VAR, MERGE, MT>), MT};
-}
-
-template <bool V, int LOGE, int LOGT>
-KernelEntry tpick(int var, bool merge) {
-  if (merge) return var ? tentry<V, LOGE, LOGT, 1, true>() : tentry<V, LOGE, LOGT, 0, true>();
-  return var ? tentry<V, LOGE, LOGT, 1, false>() : tentry<V, LOGE, LOGT, 0, false>();
-}
 
 struct Combo {
   bool v;
   int loge, logt;
 };
 constexpr Combo kCombos[] = {{false, 4, 12}, {false, 4, 13}, {false, 4, 14}, {true, 4, 12},
-                             {true, 4, 13}, {true, 5, 13}, {false, 5, 14}, {false, 5, 13}};
+                             {true, 4, 13}, {false, 5, 14}, {false, 5, 13}};
 
 }  // namespace
 
 KernelEntry tile_kernel_u32(bool has_vals, int loge, int logt, int var, bool merge) {
-  if (!has_vals && loge == 4 && logt == 12) return tpick<false, 4, 12>(var, merge);
-  if (!has_vals && loge == 4 && logt == 13) return tpick<false, 4, 13>(var, merge);
-  if (!has_vals && loge == 4 && logt == 14) return tpick<false, 4, 14>(var, merge);
-  if (has_vals && loge == 4 && logt == 12) return tpick<true, 4, 12>(var, merge);
-  if (has_vals && loge == 4 && logt == 13) return tpick<true, 4, 13>(var, merge);
-  if (has_vals && loge == 5 && logt == 13) return tpick<true, 5, 13>(var, merge);
-  if (!has_vals && loge == 5 && logt == 14) return tpick<false, 5, 14>(var, merge);
-  if (!has_vals && loge == 5 && logt == 13) return tpick<false, 5, 13>(var, merge);
+  if (has_vals) return tile_kernel_u32_pairs(loge, logt, var, merge);
+  if (loge == 4) return tile_kernel_u32_keys16(logt, var, merge);
+  if (loge == 5) return tile_kernel_u32_keys32(logt, var, merge);
   return KernelEntry{nullptr, 0};
 }
 
