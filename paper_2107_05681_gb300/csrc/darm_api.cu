@@ -409,7 +409,13 @@ int darm_bitonic_sort_host(void* keys, uint32_t* vals, size_t n, int dtype, int 
   if (m >= kHostChunkMinLog2) {
     // copies in both directions happen inside, overlapped with passes
     const int rc = sort_host_chunked(kk, dtype == DARM_F32, keys, vals, dk, dv, m, dir, variant, s);
-    if (rc != DARM_OK) return rc;
+    if (rc != DARM_OK) {
+      // copies already enqueued must not outlive the call: the workspace and
+      // the caller's buffers are reused once it returns
+      cudaStreamSynchronize(g_ctx.host_copy_stream);
+      cudaStreamSynchronize(s);
+      return rc;
+    }
     if (cudaStreamSynchronize(s) != cudaSuccess) return DARM_ERR_CUDA;
     return DARM_OK;
   }
@@ -418,7 +424,10 @@ int darm_bitonic_sort_host(void* keys, uint32_t* vals, size_t n, int dtype, int 
   if (vals && cudaMemcpyAsync(dv, vals, vbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return DARM_ERR_CUDA;
   const int rc = sort_device(kk, dtype == DARM_F32, dk, dv, n, dir, variant, s);
-  if (rc != DARM_OK) return rc;
+  if (rc != DARM_OK) {
+    cudaStreamSynchronize(s);  // let the enqueued copies finish before returning
+    return rc;
+  }
   if (cudaMemcpyAsync(keys, dk, kbytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DARM_ERR_CUDA;
   if (vals && cudaMemcpyAsync(vals, dv, vbytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return DARM_ERR_CUDA;
