@@ -191,16 +191,21 @@ def run_reference(args, world, rank):
 
 
 def kernel_sources_sha256():
-    """Hash of the CUDA sources; a recorded DRAM traffic figure is used only
-    while the kernels are unchanged since it was captured."""
+    """Hash of the pass kernels' sources and of the planner that shapes their
+    launches; a recorded DRAM traffic figure is used only while these are
+    unchanged since it was captured (host-side code such as the C ABI entry
+    points, batching and serving does not enter)."""
     import glob
     import hashlib
+    csrc = os.path.join(ROOT, "paper_2107_05681_gb300", "csrc")
+    names = ["*.cuh", "kernel_table.h", "plan.h", "plan.cu", "kernels_*.cu", "tile_*.cu",
+             "tma_*.cu", "window2*.cu"]
+    files = sorted({f for pat in names for f in glob.glob(os.path.join(csrc, pat))})
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2107_05681_gb300", "csrc", "*"))):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(os.path.basename(f).encode())
-            with open(f, "rb") as fh:
-                h.update(fh.read())
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()
 
 
