@@ -64,6 +64,10 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
                 fn = getattr(lib, name)
                 fn.argtypes = [vp, vp, vp, vp, u64, i32, vp]
                 fn.restype = i32
+            lib.oracle_oddeven_u32.argtypes = [vp, vp, u64, vp]
+            lib.oracle_oddeven_u32.restype = i32
+            lib.oracle_oddeven_rec_u32.argtypes = [vp, vp, u64]
+            lib.oracle_oddeven_rec_u32.restype = i32
             lib.oracle_compare_exchanges.argtypes = [u64]
             lib.oracle_compare_exchanges.restype = u64
             lib.oracle_mutant_id.restype = i32
@@ -142,6 +146,32 @@ def segmented_sort(keys, vals, offsets, lengths, desc=False, desc_per_seg=None,
     if rc != OK:
         raise RuntimeError(f"oracle status {rc}")
     return k, v
+
+
+def oddeven_sort(keys, vals=None, recursive=False):
+    """Sort copies of uint32 ``keys`` (and ``vals``) with Batcher's odd-even
+    merge sort network (ascending).  Returns (keys_out, vals_out or None,
+    comparators evaluated, or None for the recursive form)."""
+    k = np.ascontiguousarray(keys, dtype=np.uint32).copy()
+    if k.ndim != 1:
+        raise ValueError("keys must be 1-D")
+    v = None
+    if vals is not None:
+        v = np.ascontiguousarray(vals, dtype=np.uint32).copy()
+        if v.shape != k.shape:
+            raise ValueError("vals must match keys")
+    if recursive:
+        rc = _lib().oracle_oddeven_rec_u32(_ptr(k), _ptr(v), k.size)
+        ncmp = None
+    else:
+        c = ctypes.c_uint64(0)
+        rc = _lib().oracle_oddeven_u32(_ptr(k), _ptr(v), k.size, ctypes.byref(c))
+        ncmp = int(c.value)
+    if rc == ERR_NOT_POW2:
+        raise ValueError("length must be a power of two")
+    if rc != OK:
+        raise RuntimeError(f"oracle status {rc}")
+    return k, v, ncmp
 
 
 def compare_exchanges(n: int) -> int:

@@ -22,6 +22,8 @@
  *   - oracle_segmented_{u32,u64}: independent segments of power-of-two
  *     capacity, padded beyond their real length with the direction's
  *     extreme key before the network runs.
+ *   - oracle_oddeven_u32 / oracle_oddeven_rec_u32: Batcher's odd-even merge
+ *     sort network (PCM's base, Section VI-A), iterative and recursive.
  *
  * Readings of the paper taken here (the paper is silent on them):
  *   - descending order flips every comparator: the ascending test of Fig. 1
@@ -224,3 +226,81 @@ uint64_t oracle_compare_exchanges(uint64_t n) {
 }
 
 int oracle_mutant_id(void) { return DARM_ORACLE_MUTANT; }
+
+/*
+ * Batcher's odd-even merge sort network (the network PCM, Section VI-A, is
+ * built on), ascending, strict swaps, payload travelling with its key.
+ *
+ * Iterative form: for every merge size p = 1, 2, 4, ... < n and every
+ * distance k = p, p/2, ..., 1, x runs over [j, j + k) for
+ * j = (k mod p), (k mod p) + 2k, ..., and (x, x + k) is compared when both
+ * lie in the same block of 2p elements.  This is the textbook iterative
+ * statement of the network (Knuth, TAOCP vol. 3, 5.3.4).
+ * `ncmp` (nullable) receives the number of comparators evaluated.
+ */
+static void oe_cmpx(uint32_t* key, uint32_t* val, uint64_t a, uint64_t b) {
+  if (key[b] < key[a]) {
+    uint32_t tk = key[a];
+    key[a] = key[b];
+    key[b] = tk;
+    if (val) {
+      uint32_t tv = val[a];
+      val[a] = val[b];
+      val[b] = tv;
+    }
+  }
+}
+
+int oracle_oddeven_u32(uint32_t* key, uint32_t* val, uint64_t n, uint64_t* ncmp) {
+  uint64_t count = 0;
+  if (n > 1 && !is_pow2_u64(n)) return ORACLE_ERR_NOT_POW2;
+  for (uint64_t p = 1; p < n; p <<= 1) {
+    for (uint64_t k = p; k >= 1; k >>= 1) {
+      for (uint64_t j = k % p; j + k < n; j += 2 * k) {
+        for (uint64_t i = 0; i < k && i + j + k < n; ++i) {
+          const uint64_t x = i + j;
+          if (x / (2 * p) == (x + k) / (2 * p)) {
+            oe_cmpx(key, val, x, x + k);
+            ++count;
+          }
+        }
+      }
+    }
+  }
+  if (ncmp) *ncmp = count;
+  return ORACLE_OK;
+}
+
+/*
+ * Recursive form of the same network: sort both halves, then merge them
+ * with Batcher's odd-even merge, which merges the even- and the
+ * odd-indexed subsequences (stride 2r) recursively and then compares the
+ * neighbours (i, i + r) left out of place.  Each element meets its
+ * comparators in the same order as in the iterative form, so the results
+ * are identical, payload order under ties included.
+ */
+static void oe_merge(uint32_t* key, uint32_t* val, uint64_t lo, uint64_t n, uint64_t r) {
+  const uint64_t step = 2 * r;
+  if (step < n) {
+    oe_merge(key, val, lo, n, step);
+    oe_merge(key, val, lo + r, n, step);
+    for (uint64_t i = lo + r; i + r < lo + n; i += step) oe_cmpx(key, val, i, i + r);
+  } else {
+    oe_cmpx(key, val, lo, lo + r);
+  }
+}
+
+static void oe_sort(uint32_t* key, uint32_t* val, uint64_t lo, uint64_t n) {
+  if (n < 2) return;
+  const uint64_t h = n / 2;
+  oe_sort(key, val, lo, h);
+  oe_sort(key, val, lo + h, h);
+  oe_merge(key, val, lo, n, 1);
+}
+
+int oracle_oddeven_rec_u32(uint32_t* key, uint32_t* val, uint64_t n) {
+  if (n <= 1) return ORACLE_OK;
+  if (!is_pow2_u64(n)) return ORACLE_ERR_NOT_POW2;
+  oe_sort(key, val, 0, n);
+  return ORACLE_OK;
+}
