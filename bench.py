@@ -37,7 +37,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["darm", "reference"], default="darm")
-    ap.add_argument("--workload", choices=["kv24", "kv24skew", "f32", "cfg1", "seg", "serve"],
+    ap.add_argument("--workload",
+                    choices=["kv24", "kv24skew", "f32", "cfg1", "oem4096", "seg", "serve"],
                     default="kv24")
     ap.add_argument("--serve-requests", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -271,6 +272,94 @@ def host_cpu():
             platform.machine()}
 
 
+def run_oddeven(args, world, rank, local):
+    """Batcher's odd-even merge sort network (the base of the paper's PCM
+    benchmark) on one thread block: 4096 uniform uint32 keys, melded vs
+    divergent, L2 flushed between sorts."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2107_05681_gb300 as darm
+    import synth
+    keys = synth.cfg1_keys()
+    n = keys.size
+    src = torch.from_numpy(keys).cuda()
+    work = torch.empty_like(src)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    work.copy_(src)
+    darm.oddeven_sort_block(work)
+    torch.cuda.synchronize()
+    assert np.array_equal(work.cpu().numpy(), np.sort(keys)), "result not sorted"
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(1.0)
+    out, launches = {}, 0
+    for variant in ("melded", "divergent"):
+        for _ in range(args.warmup):
+            work.copy_(src)
+            darm.oddeven_sort_block(work, variant=variant)
+        torch.cuda.synchronize()
+        barrier(world)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        l0 = darm.launch_count()
+        for a, b in evs:
+            work.copy_(src)
+            flush.fill_(1.0)
+            a.record(stream)
+            darm.oddeven_sort_block(work, variant=variant)
+            b.record(stream)
+        torch.cuda.synchronize()
+        launches += darm.launch_count() - l0
+        out[variant] = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), world)
+    clk = clocks.stop()
+    # end to end through the binding: pinned host -> device, sort, back
+    hk = torch.empty(n, dtype=torch.uint32, pin_memory=True)
+    tot = 0.0
+    for _ in range(args.steps):
+        hk.copy_(torch.from_numpy(keys))
+        t0 = time.perf_counter()
+        work.copy_(hk, non_blocking=True)
+        darm.oddeven_sort_block(work)
+        hk.copy_(work, non_blocking=True)
+        torch.cuda.synchronize()
+        tot += time.perf_counter() - t0
+    tot = max_over_ranks(tot, world)
+    if rank == 0:
+        ms = out["melded"]
+        t0, reps = time.perf_counter(), 0
+        while time.perf_counter() - t0 < 1.0:
+            oracle.oddeven_sort(keys)
+            reps += 1
+        cdt = time.perf_counter() - t0
+        line = {
+            "metric": "sorted keys/s, melded vs divergent odd-even merge sort network; warp exec "
+                      "efficiency",
+            "value": world * n * args.steps / (ms * 1e-3), "unit": "keys/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": "Batcher odd-even merge sort network, 4096 uint32 keys "
+                                   "uniform, one thread block", "n": n, "variant": "melded",
+                       "l2": "flushed between steps (256 MiB write outside the timed events)"},
+            "divergent": {"value": world * n * args.steps / (out["divergent"] * 1e-3),
+                          "ms_per_step": out["divergent"] / args.steps},
+            "melded_over_divergent": out["divergent"] / ms,
+            "roofline": {"bound": "latency", "note": "one CTA on one SM: 78 layers, two "
+                         "barriers each; HBM and ALU peaks do not bound it"},
+            "clocks": clk, "gpu_launches": launches,
+            "e2e": {"value": world * n * args.steps / tot, "unit": "keys/s",
+                    "h2d_bytes_per_step": n * 4, "d2h_bytes_per_step": n * 4},
+            "cpu_baseline": {"value": reps * n / cdt, "unit": "keys/s", "cores": 1,
+                             "kind": "oracle", "host": host_cpu(),
+                             "sample": f"{reps} single-threaded oracle runs of the network on "
+                                       f"the same 4096 keys ({cdt:.1f} s)"},
+        }
+        print(json.dumps(line), flush=True)
+
+
 def run_segmented(args, world, rank, local):
     """Batched segmented sort: 10,000 uint32 arrays, log-uniform real lengths
     32..65536 padded to powers of two, one graph replay per step."""
@@ -428,13 +517,14 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
-    if args.workload in ("seg", "serve"):
+    if args.workload in ("seg", "serve", "oem4096"):
         import torch
 
         import paper_2107_05681_gb300 as darm
         torch.cuda.set_device(local)
         darm.init(local)
-        (run_segmented if args.workload == "seg" else run_serving)(args, world, rank, local)
+        runner = {"seg": run_segmented, "serve": run_serving, "oem4096": run_oddeven}
+        runner[args.workload](args, world, rank, local)
         return
     import numpy as np
     import torch

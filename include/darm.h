@@ -159,6 +159,20 @@ int darm_segmented_sort_noalloc(uint32_t* keys, uint32_t* vals, const uint64_t* 
                                 const uint32_t* seg_len, uint32_t num_segs, int dir,
                                 int variant, const uint8_t* seg_desc, void* stream);
 
+/* ---- Batcher's odd-even merge sort network (one thread block) ------------ */
+
+/* Sort n <= 4096 uint32 keys (power of two) ascending with Batcher's
+ * odd-even merge sort network, the network the paper's PCM benchmark builds
+ * on (Section VI-A), on one thread block in shared memory.  keys/vals are
+ * DEVICE pointers (vals nullable: keys only; a payload travels with its
+ * key; equal keys never move, so the payload order under ties is the
+ * network's).  variant: DARM_DIVERGENT (one branch per comparator end) or
+ * DARM_MELDED / DARM_AUTO (the two ends' loads and compares melded).
+ * Asynchronous on `stream`.  Errors: DARM_ERR_NOT_POW2, DARM_ERR_INVALID_ARG
+ * (n > 4096, NULL keys, bad variant), DARM_ERR_CUDA (launch). */
+int darm_oddeven_sort_block(uint32_t* keys, uint32_t* vals, size_t n, int variant,
+                            void* stream);
+
 /* ---- tuning ----------------------------------------------------------- */
 
 /* Time candidate tile sizes, elements per thread and per-stage variants for

@@ -59,6 +59,7 @@ _sig = {
     "darm_segmented_sort": ([_vp, _vp, _vp, _vp, ctypes.c_uint32, _i32, _i32, _vp, _vp], _i32),
     "darm_segmented_sort_noalloc": ([_vp, _vp, _vp, _vp, ctypes.c_uint32, _i32, _i32, _vp, _vp],
                                     _i32),
+    "darm_oddeven_sort_block": ([_vp, _vp, _sz, _i32, _vp], _i32),
     "darm_autotune": ([_i32, _sz, _i32, ctypes.c_char_p], _i32),
     "darm_autotune_segmented": ([_vp, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_char_p], _i32),
     "darm_load_tune_db": ([ctypes.c_char_p], _i32),
@@ -155,6 +156,23 @@ def sort(keys, vals=None, descending: bool = False, variant="melded", stream=Non
     else:
         raise ValueError(f"unsupported key dtype {keys.dtype}")
     _check(rc, "darm_bitonic_sort")
+
+
+def oddeven_sort_block(keys, vals=None, variant="melded", stream=None) -> None:
+    """Sort a contiguous uint32 CUDA tensor of at most 4096 keys (power of two)
+    ascending in place with Batcher's odd-even merge sort network on one
+    thread block; `vals` (uint32) travels with its key."""
+    import torch
+    if keys.dtype != torch.uint32 or not keys.is_cuda or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous uint32 CUDA tensor")
+    vp = None
+    if vals is not None:
+        if vals.dtype != torch.uint32 or vals.shape != keys.shape or not vals.is_contiguous():
+            raise ValueError("vals must be a contiguous uint32 CUDA tensor shaped like keys")
+        vp = ctypes.c_void_p(vals.data_ptr())
+    rc = lib.darm_oddeven_sort_block(ctypes.c_void_p(keys.data_ptr()), vp, keys.numel(),
+                                     _variant(variant), _stream_handle(stream))
+    _check(rc, "darm_oddeven_sort_block")
 
 
 def sort_host(keys, vals=None, descending: bool = False, variant="melded") -> None:

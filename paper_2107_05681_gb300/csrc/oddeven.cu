@@ -1,0 +1,148 @@
+// oddeven.cu - Batcher's odd-even merge sort network on one thread block, in
+// a divergent and a melded form.
+//
+// The paper's PCM benchmark (Section VI-A) is a parallel sort built on
+// Batcher's odd-even merge sort; like the bitonic kernel of Fig. 1 it runs a
+// fixed comparator network whose two sides (here: the lower and the upper
+// element of a compare-exchange) are near-identical instruction sequences
+// that diverge within a warp on thread-index bits.  This kernel sorts up to
+// 4096 uint32 keys (with an optional uint32 payload) in shared memory.
+//
+// Network (ascending, strict swaps): for p = 1, 2, 4, ... < n and
+// k = p, p/2, ..., 1, element x is
+//   - the lower end of a comparator (x, x + k) when k == p and bit p of x is
+//     clear, or when k < p, bit k of x is set and x + k stays inside x's
+//     block of 2p elements;
+//   - the upper end of (x - k, x) when k == p and bit p of x is set, or when
+//     k < p, bit k of x is clear and x - k stays inside the block;
+//   - idle otherwise.
+// Every thread updates the elements it owns: the lower end keeps the
+// smaller key, the upper end the larger, both decided by the one predicate
+// key[upper] < key[lower], so equal keys never move.  Each layer reads into
+// registers, then (after a barrier) writes back.
+//
+// Divergent form: one branch per role, each with its own partner load and
+// compare.  Melded form (the paper's region-region meld, Algorithm 2): the
+// two roles' loads are unified, the compares aligned by selecting their
+// operands, so the warp runs one copy of the body; idle elements skip it.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "darm.h"
+#include "darm_internal.h"
+
+namespace darm {
+namespace {
+
+constexpr uint32_t kOddEvenMax = 4096;
+constexpr uint32_t kOddEvenThreads = 1024;
+constexpr int kPerThread = kOddEvenMax / kOddEvenThreads;
+
+template <bool V, int VAR>
+__global__ void __launch_bounds__(kOddEvenThreads, 1)
+    darm_oddeven_block_kernel(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t n) {
+  __shared__ uint32_t sk[kOddEvenMax];
+  __shared__ uint32_t sv[V ? kOddEvenMax : 1];
+  const uint32_t tid = threadIdx.x;
+  const uint32_t nt = blockDim.x;
+  for (uint32_t x = tid; x < n; x += nt) {
+    sk[x] = keys[x];
+    if (V) sv[x] = vals[x];
+  }
+  __syncthreads();
+  for (uint32_t p = 1; p < n; p <<= 1) {
+    for (uint32_t k = p; k >= 1; k >>= 1) {
+      uint32_t nk[kPerThread], nv[kPerThread];
+#pragma unroll
+      for (int r = 0; r < kPerThread; ++r) {
+        const uint32_t x = tid + uint32_t(r) * nt;
+        if (x >= n) break;
+        const uint32_t q = x & (2 * p - 1);  // position inside the block of 2p
+        bool lower, upper;
+        if (k == p) {
+          lower = (x & p) == 0;
+          upper = !lower;
+        } else {
+          lower = (x & k) != 0 && q + k < 2 * p;
+          upper = (x & k) == 0 && q >= k;
+        }
+        uint32_t key = sk[x];
+        uint32_t val = V ? sv[x] : 0u;
+        if (VAR == 0) {
+          if (lower) {
+            const uint32_t b = sk[x + k];
+            if (b < key) {
+              key = b;
+              if (V) val = sv[x + k];
+            }
+          } else if (upper) {
+            const uint32_t a = sk[x - k];
+            if (key < a) {
+              key = a;
+              if (V) val = sv[x - k];
+            }
+          }
+        } else {
+          if (lower || upper) {
+            const uint32_t partner = lower ? x + k : x - k;
+            const uint32_t b = sk[partner];
+            const uint32_t lhs = lower ? b : key;  // key[upper]
+            const uint32_t rhs = lower ? key : b;  // key[lower]
+            if (lhs < rhs) {
+              key = b;
+              if (V) val = sv[partner];
+            }
+          }
+        }
+        nk[r] = key;
+        nv[r] = val;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < kPerThread; ++r) {
+        const uint32_t x = tid + uint32_t(r) * nt;
+        if (x >= n) break;
+        sk[x] = nk[r];
+        if (V) sv[x] = nv[r];
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t x = tid; x < n; x += nt) {
+    keys[x] = sk[x];
+    if (V) vals[x] = sv[x];
+  }
+}
+
+}  // namespace
+}  // namespace darm
+
+using namespace darm;
+
+extern "C" int darm_oddeven_sort_block(uint32_t* keys, uint32_t* vals, size_t n, int variant,
+                                       void* stream) {
+  if (!g_ctx.inited) return DARM_ERR_NOT_INIT;
+  if (variant < DARM_DIVERGENT || variant > DARM_AUTO) return DARM_ERR_INVALID_ARG;
+  if (n <= 1) return DARM_OK;
+  if ((n & (n - 1)) != 0) return DARM_ERR_NOT_POW2;
+  if (n > kOddEvenMax || !keys) return DARM_ERR_INVALID_ARG;
+  const uint32_t threads = uint32_t(n < kOddEvenThreads ? n : kOddEvenThreads);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool melded = variant != DARM_DIVERGENT;
+  const uint32_t nn = uint32_t(n);
+  if (vals) {
+    if (melded)
+      darm_oddeven_block_kernel<true, 1><<<1, threads, 0, s>>>(keys, vals, nn);
+    else
+      darm_oddeven_block_kernel<true, 0><<<1, threads, 0, s>>>(keys, vals, nn);
+  } else {
+    if (melded)
+      darm_oddeven_block_kernel<false, 1><<<1, threads, 0, s>>>(keys, nullptr, nn);
+    else
+      darm_oddeven_block_kernel<false, 0><<<1, threads, 0, s>>>(keys, nullptr, nn);
+  }
+  if (cudaGetLastError() != cudaSuccess) return DARM_ERR_CUDA;
+  g_ctx.launches.fetch_add(1, std::memory_order_relaxed);
+  return DARM_OK;
+}

@@ -4,6 +4,7 @@ profiler can capture the second sort's kernel launches.
     python -m paper_2107_05681_gb300.profile_case VARIANT WORKLOAD
 
 VARIANT: melded | divergent.  WORKLOAD: cfg1 (4096 uint32 keys, one block),
+oem4096 (the same keys through the single-block odd-even merge sort network),
 kv24 (2^24 uint32 key-value pairs), f32 (2^26 float32 keys).
 """
 import sys
@@ -17,6 +18,14 @@ import synth
 
 def main(variant="melded", workload="kv24"):
     darm.init(0)
+    if workload == "oem4096":
+        K = torch.from_numpy(synth.cfg1_keys()).cuda()
+        for _ in range(2):
+            K2 = K.clone()
+            darm.oddeven_sort_block(K2, variant=variant)
+        torch.cuda.synchronize()
+        print("ok", darm.launch_count())
+        return
     if workload == "kv24":
         k, v = synth.cfg2_kv()
     elif workload == "cfg1":

@@ -1,0 +1,52 @@
+"""GPU parity of the single-block odd-even merge sort network (both forms)
+against the oracle, bit-exact on keys and on payload order under ties."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import assert_equal, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("variant", ["divergent", "melded"])
+@pytest.mark.parametrize("m", range(1, 13))
+def test_all_sizes_with_ties(darm, m, variant):
+    import torch
+    n = 1 << m
+    keys = synth.uniform_u32(700 + m, n) % np.uint32(max(2, n // 16))
+    vals = np.arange(n, dtype=np.uint32)
+    ek, ev, _ = oracle.oddeven_sort(keys, vals)
+    k, v = to_dev(keys), to_dev(vals)
+    darm.oddeven_sort_block(k, v, variant=variant)
+    torch.cuda.synchronize()
+    assert_equal("keys", k.cpu().numpy(), ek)
+    assert_equal("payload", v.cpu().numpy(), ev)
+    k = to_dev(keys)
+    darm.oddeven_sort_block(k, variant=variant)
+    torch.cuda.synchronize()
+    assert_equal("keys only", k.cpu().numpy(), ek)
+
+
+def test_uniform_4096_both_forms_identical(darm):
+    import torch
+    keys = synth.cfg1_keys()
+    vals = np.arange(keys.size, dtype=np.uint32)
+    ek, ev, _ = oracle.oddeven_sort(keys, vals)
+    for variant in ("divergent", "melded", "auto"):
+        k, v = to_dev(keys), to_dev(vals)
+        darm.oddeven_sort_block(k, v, variant=variant)
+        torch.cuda.synchronize()
+        assert_equal(f"{variant} keys", k.cpu().numpy(), ek)
+        assert_equal(f"{variant} payload", v.cpu().numpy(), ev)
+
+
+def test_rejects_bad_sizes(darm):
+    with pytest.raises(darm.DarmError):
+        darm.oddeven_sort_block(to_dev(np.zeros(8192, np.uint32)))
+    with pytest.raises(darm.DarmError):
+        darm.oddeven_sort_block(to_dev(np.zeros(6, np.uint32)))
+    k = to_dev(np.array([5], np.uint32))
+    darm.oddeven_sort_block(k)  # n = 1: nothing to do
+    assert k.cpu().numpy().tolist() == [5]
