@@ -173,6 +173,41 @@ int darm_segmented_sort_noalloc(uint32_t* keys, uint32_t* vals, const uint64_t* 
 int darm_oddeven_sort_block(uint32_t* keys, uint32_t* vals, size_t n, int variant,
                             void* stream);
 
+/* ---- melding analysis (host only) -------------------------------------- */
+
+/* One instruction of a divergent path: `opcode` is what the frequency
+ * profile counts (an IR opcode), `type` refines it for alignment (operand
+ * types, compare predicate), `latency` its static cost.  Instructions with
+ * equal opcode must carry equal latency. */
+typedef struct {
+  int32_t opcode;
+  int32_t type;
+  int32_t latency;
+} darm_inst;
+
+/* Melding profitability of two basic blocks (Section IV-E, MP_B): the sum
+ * over opcodes of min(frequency in b1, frequency in b2) x latency, over
+ * lat(b1) + lat(b2).  Identical profiles give 0.5.  Host arrays; NaN on bad
+ * arguments or inconsistent latencies. */
+double darm_meld_mp_block(const darm_inst* b1, int n1, const darm_inst* b2, int n2);
+
+/* Melding profitability of two isomorphic subgraphs (MP_S): nb corresponding
+ * block pairs, block k of path 1 being i1[off1[k] .. off1[k+1]) (likewise
+ * path 2); the latency-weighted mean of the pairs' MP_B.  NaN on bad
+ * arguments. */
+double darm_meld_mp_subgraph(const darm_inst* i1, const int32_t* off1, const darm_inst* i2,
+                             const int32_t* off2, int nb);
+
+/* Instruction alignment of two blocks (Smith-Waterman, Section IV-E):
+ * compatible instructions (same opcode and type) align with score equal to
+ * their latency, each unaligned instruction inside the aligned stretch costs
+ * `gap` (>= 0).  Writes both sequences in program order as (i, j) pairs into
+ * `pairs` (capacity 2 * (na + nb) int32): (i, j) aligned, (i, -1) or
+ * (-1, j) unaligned.  Returns the number of pairs (-1 on bad arguments) and
+ * the alignment score in *score (nullable). */
+int darm_meld_align(const darm_inst* a, int na, const darm_inst* b, int nb, double gap,
+                    int32_t* pairs, double* score);
+
 /* ---- tuning ----------------------------------------------------------- */
 
 /* Time candidate tile sizes, elements per thread and per-stage variants for

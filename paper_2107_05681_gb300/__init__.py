@@ -60,6 +60,9 @@ _sig = {
     "darm_segmented_sort_noalloc": ([_vp, _vp, _vp, _vp, ctypes.c_uint32, _i32, _i32, _vp, _vp],
                                     _i32),
     "darm_oddeven_sort_block": ([_vp, _vp, _sz, _i32, _vp], _i32),
+    "darm_meld_mp_block": ([_vp, _i32, _vp, _i32], ctypes.c_double),
+    "darm_meld_mp_subgraph": ([_vp, _vp, _vp, _vp, _i32], ctypes.c_double),
+    "darm_meld_align": ([_vp, _i32, _vp, _i32, ctypes.c_double, _vp, _vp], _i32),
     "darm_autotune": ([_i32, _sz, _i32, ctypes.c_char_p], _i32),
     "darm_autotune_segmented": ([_vp, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_char_p], _i32),
     "darm_load_tune_db": ([ctypes.c_char_p], _i32),
@@ -173,6 +176,52 @@ def oddeven_sort_block(keys, vals=None, variant="melded", stream=None) -> None:
     rc = lib.darm_oddeven_sort_block(ctypes.c_void_p(keys.data_ptr()), vp, keys.numel(),
                                      _variant(variant), _stream_handle(stream))
     _check(rc, "darm_oddeven_sort_block")
+
+
+# ---- melding analysis (host only) ----------------------------------------------
+
+def _insts(seq):
+    """[(opcode, type, latency), ...] -> contiguous int32 array of darm_inst."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(seq, dtype=np.int32).reshape(-1, 3))
+    return a, (a.ctypes.data_as(ctypes.c_void_p) if a.size else None)
+
+
+def meld_mp_block(b1, b2) -> float:
+    """MP_B of two basic blocks given as [(opcode, type, latency), ...]."""
+    a1, p1 = _insts(b1)
+    a2, p2 = _insts(b2)
+    return float(lib.darm_meld_mp_block(p1, len(a1), p2, len(a2)))
+
+
+def meld_mp_subgraph(blocks1, blocks2) -> float:
+    """MP_S of two subgraphs given as lists of corresponding blocks."""
+    import numpy as np
+    if len(blocks1) != len(blocks2) or not blocks1:
+        raise ValueError("subgraphs must have the same, non-zero number of blocks")
+    off1 = np.cumsum([0] + [len(b) for b in blocks1]).astype(np.int32)
+    off2 = np.cumsum([0] + [len(b) for b in blocks2]).astype(np.int32)
+    a1, p1 = _insts([i for b in blocks1 for i in b])
+    a2, p2 = _insts([i for b in blocks2 for i in b])
+    return float(lib.darm_meld_mp_subgraph(p1, off1.ctypes.data_as(ctypes.c_void_p), p2,
+                                           off2.ctypes.data_as(ctypes.c_void_p), len(blocks1)))
+
+
+def meld_align(a, b, gap: float = 1.0):
+    """Smith-Waterman instruction alignment of two blocks: returns
+    ([(i or None, j or None), ...] in program order, score)."""
+    import numpy as np
+    aa, pa = _insts(a)
+    ab, pb = _insts(b)
+    pairs = np.zeros(2 * (len(aa) + len(ab)) + 2, dtype=np.int32)
+    score = ctypes.c_double(0.0)
+    n = lib.darm_meld_align(pa, len(aa), pb, len(ab), float(gap),
+                            pairs.ctypes.data_as(ctypes.c_void_p), ctypes.byref(score))
+    if n < 0:
+        raise ValueError("bad alignment arguments")
+    out = [(None if x < 0 else int(x), None if y < 0 else int(y))
+           for x, y in pairs[: 2 * n].reshape(-1, 2)]
+    return out, float(score.value)
 
 
 def sort_host(keys, vals=None, descending: bool = False, variant="melded") -> None:
