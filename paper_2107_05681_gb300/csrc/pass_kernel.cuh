@@ -123,14 +123,6 @@ struct PassParams {
 // helpers
 // ---------------------------------------------------------------------------
 
-// Shared-memory address swizzle: fold the higher index bits onto the five
-// bank bits with XOR.  It is linear over GF(2), so
-// swz(x | y) == swz(x) ^ swz(y) for disjoint x, y, and a bijection on any
-// power-of-two range.
-__device__ __forceinline__ uint32_t swz(uint32_t x) {
-  return x ^ (((x >> 5) ^ (x >> 10) ^ (x >> 15)) & 31u);
-}
-
 template <typename K>
 __device__ __forceinline__ K key_in(K x, uint32_t f);
 template <typename K>

@@ -135,7 +135,6 @@ struct Interleave {
   static constexpr bool value = V && sizeof(K) == 4;
 };
 __host__ __device__ constexpr uint32_t phys8_c(uint32_t l) { return l + ((l >> 4) << 1); }
-__host__ __device__ constexpr uint32_t phys_c(uint32_t l) { return l + ((l >> 5) << 2); }
 
 // Pad words per 32 elements of the tile kernels' own shared memory.  Tiles
 // of 32-bit keys without payload and 32 keys per thread pad one word per 32
