@@ -38,7 +38,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["darm", "reference"], default="darm")
     ap.add_argument("--workload",
-                    choices=["kv24", "kv24skew", "f32", "cfg1", "oem4096", "seg", "serve"],
+                    choices=["kv24", "kv24skew", "f32", "cfg1", "oem4096", "oem26", "seg",
+                             "serve"],
                     default="kv24")
     ap.add_argument("--serve-requests", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -221,6 +222,16 @@ def recorded_traffic(workload_name, pass_kind):
     return rec.get(workload_name, {}).get(pass_kind)
 
 
+def measured_hbm_peak():
+    """HBM copy bandwidth (GB/s) measured on this machine's GPUs, else the
+    earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
 def cpu_baseline(keys, vals):
     """Oracle keys/s on a bounded sample (about 10-20 s of one core)."""
     import numpy as np
@@ -274,24 +285,37 @@ def host_cpu():
 
 def run_oddeven(args, world, rank, local):
     """Batcher's odd-even merge sort network (the base of the paper's PCM
-    benchmark) on one thread block: 4096 uniform uint32 keys, melded vs
-    divergent, L2 flushed between sorts."""
+    benchmark), melded vs divergent, L2 flushed between sorts: one thread
+    block on 4096 uniform uint32 keys (oem4096), or 2^26 uniform uint32 keys
+    sorted bucket by bucket, 4096 keys per thread block (oem26, the paper's
+    way of running its benchmarks on a 2^26-element input)."""
     import numpy as np
     import torch
 
     import oracle
     import paper_2107_05681_gb300 as darm
     import synth
-    keys = synth.cfg1_keys()
+    bucket = 4096
+    if args.workload == "oem26":
+        keys = synth.uniform_u32(0xDA2C0006, 1 << 26)
+        what = ("Batcher odd-even merge sort network, 2^26 uint32 keys uniform, sorted in "
+                "buckets of 4096 keys, one thread block per bucket")
+    else:
+        keys = synth.cfg1_keys()
+        what = "Batcher odd-even merge sort network, 4096 uint32 keys uniform, one thread block"
     n = keys.size
     src = torch.from_numpy(keys).cuda()
     work = torch.empty_like(src)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    def run_sort(t, variant="melded"):
+        darm.oddeven_sort_buckets(t, bucket=bucket, variant=variant)
+
     work.copy_(src)
-    darm.oddeven_sort_block(work)
+    run_sort(work)
     torch.cuda.synchronize()
-    assert np.array_equal(work.cpu().numpy(), np.sort(keys)), "result not sorted"
+    got = work.cpu().numpy().reshape(-1, bucket)
+    assert np.all(got[:, 1:] >= got[:, :-1]), "a bucket is not sorted"
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(1.0)
@@ -299,7 +323,7 @@ def run_oddeven(args, world, rank, local):
     for variant in ("melded", "divergent"):
         for _ in range(args.warmup):
             work.copy_(src)
-            darm.oddeven_sort_block(work, variant=variant)
+            run_sort(work, variant)
         torch.cuda.synchronize()
         barrier(world)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -309,7 +333,7 @@ def run_oddeven(args, world, rank, local):
             work.copy_(src)
             flush.fill_(1.0)
             a.record(stream)
-            darm.oddeven_sort_block(work, variant=variant)
+            run_sort(work, variant)
             b.record(stream)
         torch.cuda.synchronize()
         launches += darm.launch_count() - l0
@@ -322,16 +346,27 @@ def run_oddeven(args, world, rank, local):
         hk.copy_(torch.from_numpy(keys))
         t0 = time.perf_counter()
         work.copy_(hk, non_blocking=True)
-        darm.oddeven_sort_block(work)
+        run_sort(work)
         hk.copy_(work, non_blocking=True)
         torch.cuda.synchronize()
         tot += time.perf_counter() - t0
     tot = max_over_ranks(tot, world)
     if rank == 0:
         ms = out["melded"]
+        if n > bucket:
+            # every key is read and written once: 8 bytes per key per sort
+            ach = 8.0 * n * args.steps / (ms * 1e-3) / 1e9
+            peak = measured_hbm_peak()
+            roof = {"bound": "shared memory + barriers (78 layers per bucket)",
+                    "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                    "traffic": None, "note": "HBM traffic of one sort: one read and one write "
+                    "of each key; the time is the buckets' in-block layers"}
+        else:
+            roof = {"bound": "latency", "note": "one CTA on one SM: 78 layers, two barriers "
+                    "each; HBM and ALU peaks do not bound it"}
         t0, reps = time.perf_counter(), 0
-        while time.perf_counter() - t0 < 1.0:
-            oracle.oddeven_sort(keys)
+        while time.perf_counter() - t0 < 1.0:  # one bucket per oracle call
+            oracle.oddeven_sort(keys[(reps % (n // bucket)) * bucket:][:bucket])
             reps += 1
         cdt = time.perf_counter() - t0
         line = {
@@ -341,21 +376,19 @@ def run_oddeven(args, world, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": {"workload": "Batcher odd-even merge sort network, 4096 uint32 keys "
-                                   "uniform, one thread block", "n": n, "variant": "melded",
+            "config": {"workload": what, "n": n, "bucket": bucket, "variant": "melded",
                        "l2": "flushed between steps (256 MiB write outside the timed events)"},
             "divergent": {"value": world * n * args.steps / (out["divergent"] * 1e-3),
                           "ms_per_step": out["divergent"] / args.steps},
             "melded_over_divergent": out["divergent"] / ms,
-            "roofline": {"bound": "latency", "note": "one CTA on one SM: 78 layers, two "
-                         "barriers each; HBM and ALU peaks do not bound it"},
+            "roofline": roof,
             "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": world * n * args.steps / tot, "unit": "keys/s",
                     "h2d_bytes_per_step": n * 4, "d2h_bytes_per_step": n * 4},
-            "cpu_baseline": {"value": reps * n / cdt, "unit": "keys/s", "cores": 1,
+            "cpu_baseline": {"value": reps * bucket / cdt, "unit": "keys/s", "cores": 1,
                              "kind": "oracle", "host": host_cpu(),
-                             "sample": f"{reps} single-threaded oracle runs of the network on "
-                                       f"the same 4096 keys ({cdt:.1f} s)"},
+                             "sample": f"{reps} single-threaded oracle runs of the network, "
+                                       f"one {bucket}-key bucket each ({cdt:.1f} s)"},
         }
         print(json.dumps(line), flush=True)
 
@@ -517,13 +550,14 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
-    if args.workload in ("seg", "serve", "oem4096"):
+    if args.workload in ("seg", "serve", "oem4096", "oem26"):
         import torch
 
         import paper_2107_05681_gb300 as darm
         torch.cuda.set_device(local)
         darm.init(local)
-        runner = {"seg": run_segmented, "serve": run_serving, "oem4096": run_oddeven}
+        runner = {"seg": run_segmented, "serve": run_serving, "oem4096": run_oddeven,
+                  "oem26": run_oddeven}
         runner[args.workload](args, world, rank, local)
         return
     import numpy as np

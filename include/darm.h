@@ -173,6 +173,15 @@ int darm_segmented_sort_noalloc(uint32_t* keys, uint32_t* vals, const uint64_t* 
 int darm_oddeven_sort_block(uint32_t* keys, uint32_t* vals, size_t n, int variant,
                             void* stream);
 
+/* The same network on every aligned bucket of `bucket` keys (a power of two,
+ * <= 4096) of an array of n keys (a multiple of `bucket`), one thread block
+ * per bucket: the way the paper's benchmarks sort their input bucket by
+ * bucket (Section VI-A).  Each bucket is sorted ascending on its own.
+ * Errors: DARM_ERR_NOT_POW2 (bucket), DARM_ERR_INVALID_ARG (bucket > 4096,
+ * n not a multiple of bucket, NULL keys, bad variant), DARM_ERR_CUDA. */
+int darm_oddeven_sort_buckets(uint32_t* keys, uint32_t* vals, size_t n, size_t bucket,
+                              int variant, void* stream);
+
 /* ---- melding analysis (host only) -------------------------------------- */
 
 /* One instruction of a divergent path: `opcode` is what the frequency

@@ -60,6 +60,7 @@ _sig = {
     "darm_segmented_sort_noalloc": ([_vp, _vp, _vp, _vp, ctypes.c_uint32, _i32, _i32, _vp, _vp],
                                     _i32),
     "darm_oddeven_sort_block": ([_vp, _vp, _sz, _i32, _vp], _i32),
+    "darm_oddeven_sort_buckets": ([_vp, _vp, _sz, _sz, _i32, _vp], _i32),
     "darm_meld_mp_block": ([_vp, _i32, _vp, _i32], ctypes.c_double),
     "darm_meld_mp_subgraph": ([_vp, _vp, _vp, _vp, _i32], ctypes.c_double),
     "darm_meld_align": ([_vp, _i32, _vp, _i32, ctypes.c_double, _vp, _vp], _i32),
@@ -222,6 +223,24 @@ def meld_align(a, b, gap: float = 1.0):
     out = [(None if x < 0 else int(x), None if y < 0 else int(y))
            for x, y in pairs[: 2 * n].reshape(-1, 2)]
     return out, float(score.value)
+
+
+def oddeven_sort_buckets(keys, vals=None, bucket: int = 4096, variant="melded",
+                         stream=None) -> None:
+    """Sort every aligned bucket of `bucket` keys (power of two, <= 4096) of a
+    contiguous uint32 CUDA tensor in place with the odd-even merge sort
+    network, one thread block per bucket."""
+    import torch
+    if keys.dtype != torch.uint32 or not keys.is_cuda or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous uint32 CUDA tensor")
+    vp = None
+    if vals is not None:
+        if vals.dtype != torch.uint32 or vals.shape != keys.shape or not vals.is_contiguous():
+            raise ValueError("vals must be a contiguous uint32 CUDA tensor shaped like keys")
+        vp = ctypes.c_void_p(vals.data_ptr())
+    rc = lib.darm_oddeven_sort_buckets(ctypes.c_void_p(keys.data_ptr()), vp, keys.numel(),
+                                       int(bucket), _variant(variant), _stream_handle(stream))
+    _check(rc, "darm_oddeven_sort_buckets")
 
 
 def sort_host(keys, vals=None, descending: bool = False, variant="melded") -> None:

@@ -6,7 +6,9 @@
 // fixed comparator network whose two sides (here: the lower and the upper
 // element of a compare-exchange) are near-identical instruction sequences
 // that diverge within a warp on thread-index bits.  This kernel sorts up to
-// 4096 uint32 keys (with an optional uint32 payload) in shared memory.
+// 4096 uint32 keys (with an optional uint32 payload) in shared memory; a
+// grid of such blocks sorts an array bucket by bucket, the way the paper's
+// benchmarks sort their 2^26-element input (one bucket per thread block).
 //
 // Network (ascending, strict swaps): for p = 1, 2, 4, ... < n and
 // k = p, p/2, ..., 1, element x is
@@ -39,9 +41,12 @@ constexpr uint32_t kOddEvenMax = 4096;
 constexpr uint32_t kOddEvenThreads = 1024;
 constexpr int kPerThread = kOddEvenMax / kOddEvenThreads;
 
+// Block b sorts keys[b*n .. (b+1)*n) (and the same payload range).
 template <bool V, int VAR>
 __global__ void __launch_bounds__(kOddEvenThreads, 1)
     darm_oddeven_block_kernel(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t n) {
+  keys += size_t(blockIdx.x) * n;
+  if (V) vals += size_t(blockIdx.x) * n;
   __shared__ uint32_t sk[kOddEvenMax];
   __shared__ uint32_t sv[V ? kOddEvenMax : 1];
   const uint32_t tid = threadIdx.x;
@@ -120,29 +125,39 @@ __global__ void __launch_bounds__(kOddEvenThreads, 1)
 
 using namespace darm;
 
-extern "C" int darm_oddeven_sort_block(uint32_t* keys, uint32_t* vals, size_t n, int variant,
-                                       void* stream) {
+extern "C" int darm_oddeven_sort_buckets(uint32_t* keys, uint32_t* vals, size_t n,
+                                         size_t bucket, int variant, void* stream) {
   if (!g_ctx.inited) return DARM_ERR_NOT_INIT;
   if (variant < DARM_DIVERGENT || variant > DARM_AUTO) return DARM_ERR_INVALID_ARG;
-  if (n <= 1) return DARM_OK;
-  if ((n & (n - 1)) != 0) return DARM_ERR_NOT_POW2;
-  if (n > kOddEvenMax || !keys) return DARM_ERR_INVALID_ARG;
-  const uint32_t threads = uint32_t(n < kOddEvenThreads ? n : kOddEvenThreads);
+  if (n == 0) return DARM_OK;
+  if (bucket == 0 || (bucket & (bucket - 1)) != 0) return DARM_ERR_NOT_POW2;
+  if (bucket > kOddEvenMax || n % bucket != 0 || !keys) return DARM_ERR_INVALID_ARG;
+  if (n / bucket > size_t(0x7FFFFFFF)) return DARM_ERR_INVALID_ARG;
+  if (bucket == 1) return DARM_OK;
+  const uint32_t threads = uint32_t(bucket < kOddEvenThreads ? bucket : kOddEvenThreads);
+  const dim3 grid(uint32_t(n / bucket));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool melded = variant != DARM_DIVERGENT;
-  const uint32_t nn = uint32_t(n);
+  const uint32_t nb = uint32_t(bucket);
   if (vals) {
     if (melded)
-      darm_oddeven_block_kernel<true, 1><<<1, threads, 0, s>>>(keys, vals, nn);
+      darm_oddeven_block_kernel<true, 1><<<grid, threads, 0, s>>>(keys, vals, nb);
     else
-      darm_oddeven_block_kernel<true, 0><<<1, threads, 0, s>>>(keys, vals, nn);
+      darm_oddeven_block_kernel<true, 0><<<grid, threads, 0, s>>>(keys, vals, nb);
   } else {
     if (melded)
-      darm_oddeven_block_kernel<false, 1><<<1, threads, 0, s>>>(keys, nullptr, nn);
+      darm_oddeven_block_kernel<false, 1><<<grid, threads, 0, s>>>(keys, nullptr, nb);
     else
-      darm_oddeven_block_kernel<false, 0><<<1, threads, 0, s>>>(keys, nullptr, nn);
+      darm_oddeven_block_kernel<false, 0><<<grid, threads, 0, s>>>(keys, nullptr, nb);
   }
   if (cudaGetLastError() != cudaSuccess) return DARM_ERR_CUDA;
   g_ctx.launches.fetch_add(1, std::memory_order_relaxed);
   return DARM_OK;
+}
+
+extern "C" int darm_oddeven_sort_block(uint32_t* keys, uint32_t* vals, size_t n, int variant,
+                                       void* stream) {
+  if (n <= 1) return g_ctx.inited ? DARM_OK : DARM_ERR_NOT_INIT;
+  if ((n & (n - 1)) != 0) return g_ctx.inited ? DARM_ERR_NOT_POW2 : DARM_ERR_NOT_INIT;
+  return darm_oddeven_sort_buckets(keys, vals, n, n, variant, stream);
 }

@@ -5,6 +5,7 @@ profiler can capture the second sort's kernel launches.
 
 VARIANT: melded | divergent.  WORKLOAD: cfg1 (4096 uint32 keys, one block),
 oem4096 (the same keys through the single-block odd-even merge sort network),
+oem26 (2^26 uint32 keys through that network in buckets of 4096, one block each),
 kv24 (2^24 uint32 key-value pairs), f32 (2^26 float32 keys).
 """
 import sys
@@ -18,11 +19,12 @@ import synth
 
 def main(variant="melded", workload="kv24"):
     darm.init(0)
-    if workload == "oem4096":
-        K = torch.from_numpy(synth.cfg1_keys()).cuda()
+    if workload in ("oem4096", "oem26"):
+        keys = synth.cfg1_keys() if workload == "oem4096" else synth.uniform_u32(0xDA2C0006, 1 << 26)
+        K = torch.from_numpy(keys).cuda()
         for _ in range(2):
             K2 = K.clone()
-            darm.oddeven_sort_block(K2, variant=variant)
+            darm.oddeven_sort_buckets(K2, bucket=4096, variant=variant)
         torch.cuda.synchronize()
         print("ok", darm.launch_count())
         return

@@ -29,10 +29,16 @@ def test_binding_covers_the_header():
 
 
 def test_status_strings_and_uninitialised_calls():
+    import subprocess
+    import sys
     import paper_2107_05681_gb300 as darm
     assert darm.status_str(darm.OK) == "DARM_OK"
     assert darm.status_str(darm.ERR_NOT_POW2) == "DARM_ERR_NOT_POW2"
     assert darm.status_str(12345) == "DARM_ERR_UNKNOWN"
-    # before darm_sort_init every sorting call is refused on the host
-    assert darm.lib.darm_bitonic_sort(None, None, 16, 0, 1, None) == darm.ERR_NOT_INIT
-    assert darm.lib.darm_launch_count() == 0
+    # before darm_sort_init every sorting call is refused on the host (in a
+    # fresh process: other tests may have initialised this one)
+    code = ("import paper_2107_05681_gb300 as d; "
+            "assert d.lib.darm_bitonic_sort(None, None, 16, 0, 1, None) == d.ERR_NOT_INIT; "
+            "assert d.lib.darm_oddeven_sort_block(None, None, 16, 1, None) == d.ERR_NOT_INIT; "
+            "assert d.lib.darm_launch_count() == 0")
+    subprocess.run([sys.executable, "-c", code], cwd=ROOT, check=True)

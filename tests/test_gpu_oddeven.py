@@ -50,3 +50,31 @@ def test_rejects_bad_sizes(darm):
     k = to_dev(np.array([5], np.uint32))
     darm.oddeven_sort_block(k)  # n = 1: nothing to do
     assert k.cpu().numpy().tolist() == [5]
+
+
+@pytest.mark.parametrize("variant", ["divergent", "melded"])
+@pytest.mark.parametrize("bucket", [2, 256, 4096])
+def test_buckets_each_sorted_like_the_oracle(darm, bucket, variant):
+    """One thread block per bucket: every bucket equals the oracle's sort of
+    that bucket alone, payload order included."""
+    import torch
+    n = 1 << 18
+    keys = synth.uniform_u32(800 + bucket, n) % np.uint32(512)
+    vals = np.arange(n, dtype=np.uint32)
+    k, v = to_dev(keys), to_dev(vals)
+    darm.oddeven_sort_buckets(k, v, bucket=bucket, variant=variant)
+    torch.cuda.synchronize()
+    gk, gv = k.cpu().numpy(), v.cpu().numpy()
+    for b in range(0, n, max(bucket, n // 64)):  # a spread of buckets
+        ek, ev, _ = oracle.oddeven_sort(keys[b:b + bucket], vals[b:b + bucket])
+        assert_equal(f"keys of bucket at {b}", gk[b:b + bucket], ek)
+        assert_equal(f"payload of bucket at {b}", gv[b:b + bucket], ev)
+
+
+def test_bucket_arguments_are_checked(darm):
+    k = to_dev(np.zeros(1 << 12, np.uint32))
+    for bucket in (3, 8192):
+        with pytest.raises(darm.DarmError):
+            darm.oddeven_sort_buckets(k, bucket=bucket)
+    with pytest.raises(darm.DarmError):
+        darm.oddeven_sort_buckets(to_dev(np.zeros(6000, np.uint32)), bucket=4096)
