@@ -74,7 +74,8 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"darm_bench_clocks_rank{device_index}.csv")
 
     def start(self):
         try:
