@@ -68,6 +68,8 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
             lib.oracle_oddeven_u32.restype = i32
             lib.oracle_oddeven_rec_u32.argtypes = [vp, vp, u64]
             lib.oracle_oddeven_rec_u32.restype = i32
+            lib.oracle_sb.argtypes = [i32, vp, u64, i32, i32]
+            lib.oracle_sb.restype = i32
             lib.oracle_compare_exchanges.argtypes = [u64]
             lib.oracle_compare_exchanges.restype = u64
             lib.oracle_mutant_id.restype = i32
@@ -172,6 +174,21 @@ def oddeven_sort(keys, vals=None, recursive=False):
     if rc != OK:
         raise RuntimeError(f"oracle status {rc}")
     return k, v, ncmp
+
+
+SB_PATTERNS = {"SB1": 1, "SB4": 4, "SB1-R": 101, "SB4-R": 104}
+
+
+def sb_run(pattern: str, data, iters: int, rounds: int):
+    """The synthetic divergent kernels (see oracle_sb in darm_oracle.c) on a
+    copy of ``data`` (uint32, a multiple of 1024 words: one block each)."""
+    d = np.ascontiguousarray(data, dtype=np.uint32).copy()
+    if d.size % 1024:
+        raise ValueError("data must hold whole blocks of 1024 words")
+    rc = _lib().oracle_sb(SB_PATTERNS[pattern], _ptr(d), d.size // 1024, int(iters), int(rounds))
+    if rc != OK:
+        raise ValueError(f"bad pattern {pattern}")
+    return d
 
 
 def compare_exchanges(n: int) -> int:

@@ -24,6 +24,7 @@
  *     extreme key before the network runs.
  *   - oracle_oddeven_u32 / oracle_oddeven_rec_u32: Batcher's odd-even merge
  *     sort network (PCM's base, Section VI-A), iterative and recursive.
+ *   - oracle_sb: the synthetic divergent kernels SB1, SB4, SB1-R, SB4-R.
  *
  * Readings of the paper taken here (the paper is silent on them):
  *   - descending order flips every comparator: the ascending test of Fig. 1
@@ -303,4 +304,60 @@ int oracle_oddeven_rec_u32(uint32_t* key, uint32_t* val, uint64_t n) {
   if (!is_pow2_u64(n)) return ORACLE_ERR_NOT_POW2;
   oe_sort(key, val, 0, n);
   return ORACLE_OK;
+}
+
+/*
+ * Synthetic divergent kernels SB1, SB4 and their -R variants (Section VI-A:
+ * two nested loops whose inner loop holds a divergent region; every path
+ * works on different data of the thread's shared-memory slice; SB1 is a
+ * two-way diamond, SB4 a three-way if-else-if-else; in SB1/SB4 the paths
+ * compute identically, in the -R variants they do not).  The paper's figure
+ * with their exact code is lost; this is the form the library implements:
+ *
+ *   block of 256 threads, thread t owns words s[q] = data[blk*1024 + q*256 + t],
+ *   q = 0..3; for it in [0, iters), for j in [0, 4):
+ *     SB1:  c = (t ^ j ^ it) & 1;  c == 1: (a, b) = (j, j+1), else (j+2, j+3)
+ *     SB4:  c = (t + j + it) % 3;  (a, b) = (j + c, j + c + 1)
+ *     (indices mod 4); then R rounds of  s[a] = g(s[a], s[b]):
+ *       identical paths:  g(v, w) = 3v + w
+ *       -R paths:         c = 0: 3v + w,  c = 1: 5v ^ w,  c = 2: 7v - w
+ *   (all arithmetic modulo 2^32).
+ * pattern: 1 SB1, 4 SB4, 101 SB1-R, 104 SB4-R.  Status 1 on a bad pattern.
+ */
+int oracle_sb(int pattern, uint32_t* data, uint64_t nblocks, int iters, int rounds) {
+  if (pattern != 1 && pattern != 4 && pattern != 101 && pattern != 104) return 1;
+  const int three_way = (pattern == 4 || pattern == 104);
+  const int same = (pattern < 100);
+  for (uint64_t blk = 0; blk < nblocks; ++blk) {
+    uint32_t* d = data + blk * 1024;
+    for (uint32_t t = 0; t < 256; ++t) {
+      uint32_t s[4];
+      for (int q = 0; q < 4; ++q) s[q] = d[q * 256 + t];
+      for (int it = 0; it < iters; ++it) {
+        for (uint32_t j = 0; j < 4; ++j) {
+          uint32_t c, a, b;
+          if (three_way) {
+            c = (t + j + (uint32_t)it) % 3u;
+            a = (j + c) & 3u;
+          } else {
+            c = (t ^ j ^ (uint32_t)it) & 1u;
+            a = c ? j : ((j + 2) & 3u);
+            c = c ? 0u : 1u; /* path index: 0 = first path, 1 = second */
+          }
+          b = (a + 1) & 3u;
+          for (int r = 0; r < rounds; ++r) {
+            const uint32_t v = s[a], w = s[b];
+            if (same || c == 0)
+              s[a] = 3u * v + w;
+            else if (c == 1)
+              s[a] = (5u * v) ^ w;
+            else
+              s[a] = 7u * v - w;
+          }
+        }
+      }
+      for (int q = 0; q < 4; ++q) d[q * 256 + t] = s[q];
+    }
+  }
+  return 0;
 }
