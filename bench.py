@@ -38,8 +38,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["darm", "reference"], default="darm")
     ap.add_argument("--workload",
-                    choices=["kv24", "kv24skew", "f32", "cfg1", "oem4096", "oem26", "seg",
-                             "serve"],
+                    choices=["kv24", "kv24skew", "f32", "cfg1", "oem4096", "oem26", "sb",
+                             "seg", "serve"],
                     default="kv24")
     ap.add_argument("--serve-requests", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -394,6 +394,106 @@ def run_oddeven(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_synthetic(args, world, rank, local):
+    """The synthetic divergent kernels SB1, SB4, SB1-R, SB4-R (Section VI-A),
+    melded vs divergent: 1216 blocks of 256 threads (eight per SM), 64 outer
+    iterations of 4 divergent inner steps, 32 compute rounds per path."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2107_05681_gb300 as darm
+    import synth
+    nblocks, iters, rounds = 152 * 8, 64, 32
+    src = torch.from_numpy(synth.uniform_u32(0xDA2C0007, 1024 * nblocks)).cuda()
+    work = torch.empty_like(src)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    # correctness guard: the first 8 blocks against the oracle
+    sample = src[: 8 * 1024].cpu().numpy()
+    for pat in darm.SB_PATTERNS:
+        work.copy_(src)
+        darm.sb_run(pat, work, iters, rounds)
+        torch.cuda.synchronize()
+        assert np.array_equal(work[: 8 * 1024].cpu().numpy(),
+                              oracle.sb_run(pat, sample, iters, rounds)), pat
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(1.0)
+    res, launches = {}, 0
+    for pat in darm.SB_PATTERNS:
+        res[pat] = {}
+        for variant in ("melded", "divergent"):
+            for _ in range(args.warmup):
+                work.copy_(src)
+                darm.sb_run(pat, work, iters, rounds, variant=variant)
+            torch.cuda.synchronize()
+            barrier(world)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            l0 = darm.launch_count()
+            for a, b in evs:
+                work.copy_(src)
+                flush.fill_(1.0)
+                a.record(stream)
+                darm.sb_run(pat, work, iters, rounds, variant=variant)
+                b.record(stream)
+            torch.cuda.synchronize()
+            launches += darm.launch_count() - l0
+            res[pat][variant] = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs),
+                                               world) / args.steps
+    clk = clocks.stop()
+    speedups = {p: r["divergent"] / r["melded"] for p, r in res.items()}
+    geo = math.exp(sum(math.log(v) for v in speedups.values()) / len(speedups))
+    # end to end: copy in, all four kernels (melded), copy back
+    hk = torch.empty(src.numel(), dtype=torch.uint32, pin_memory=True)
+    hk.copy_(src.cpu())
+    tot = 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        work.copy_(hk, non_blocking=True)
+        for pat in darm.SB_PATTERNS:
+            darm.sb_run(pat, work, iters, rounds)
+        hk.copy_(work, non_blocking=True)
+        torch.cuda.synchronize()
+        tot += time.perf_counter() - t0
+    tot = max_over_ranks(tot, world)
+    if rank == 0:
+        t0, reps = time.perf_counter(), 0
+        while time.perf_counter() - t0 < 1.0:
+            oracle.sb_run("SB1", sample[:1024], iters, rounds)
+            reps += 1
+        cdt = time.perf_counter() - t0
+        per_block_steps = 256 * iters * 4  # thread inner steps per block
+        line = {
+            "metric": "synthetic divergent kernels: melded over divergent speedup (geomean of "
+                      "SB1, SB4, SB1-R, SB4-R); warp exec efficiency",
+            "value": geo, "unit": "x", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(r["melded"] for r in res.values()),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": "synthetic divergent kernels SB1, SB4, SB1-R, SB4-R, "
+                                   f"{nblocks} blocks x 256 threads, {iters} outer iterations, "
+                                   f"4 divergent inner steps, {rounds} rounds per path",
+                       "l2": "flushed between steps (256 MiB write outside the timed events)"},
+            "per_kernel_ms": res, "speedup": speedups,
+            "paper_context": "DARM on an AMD Vega 20: 1.36x geomean over SB1-SB4(-R)",
+            "roofline": {"bound": "alu", "note": "compute rounds in registers; shared memory "
+                         "traffic 2 loads + 1 store per path step"},
+            "clocks": clk, "gpu_launches": launches,
+            "e2e": {"value": world * nblocks * per_block_steps * 4 * args.steps / tot,
+                    "unit": "thread inner steps/s (all four kernels, copies included)",
+                    "h2d_bytes_per_step": src.numel() * 4, "d2h_bytes_per_step": src.numel() * 4},
+            "cpu_baseline": {"value": reps * per_block_steps / cdt,
+                             "unit": "thread inner steps/s (SB1)", "cores": 1, "kind": "oracle",
+                             "host": host_cpu(),
+                             "sample": f"{reps} oracle runs of SB1 on one block ({cdt:.1f} s)"},
+        }
+        print(json.dumps(line), flush=True)
+
+
 def run_segmented(args, world, rank, local):
     """Batched segmented sort: 10,000 uint32 arrays, log-uniform real lengths
     32..65536 padded to powers of two, one graph replay per step."""
@@ -551,14 +651,14 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
-    if args.workload in ("seg", "serve", "oem4096", "oem26"):
+    if args.workload in ("seg", "serve", "oem4096", "oem26", "sb"):
         import torch
 
         import paper_2107_05681_gb300 as darm
         torch.cuda.set_device(local)
         darm.init(local)
         runner = {"seg": run_segmented, "serve": run_serving, "oem4096": run_oddeven,
-                  "oem26": run_oddeven}
+                  "oem26": run_oddeven, "sb": run_synthetic}
         runner[args.workload](args, world, rank, local)
         return
     import numpy as np

@@ -182,6 +182,22 @@ int darm_oddeven_sort_block(uint32_t* keys, uint32_t* vals, size_t n, int varian
 int darm_oddeven_sort_buckets(uint32_t* keys, uint32_t* vals, size_t n, size_t bucket,
                               int variant, void* stream);
 
+/* ---- synthetic divergent kernels (Section VI-A) ------------------------- */
+
+/* The paper's synthetic kernels, as built here: two nested loops whose inner
+ * loop holds a divergent region; each path works on different words of the
+ * thread's shared-memory slice.  pattern: 1 = SB1 (two-way diamond, paths
+ * compute identically), 4 = SB4 (three-way if-else-if-else, identical),
+ * 101 = SB1-R, 104 = SB4-R (paths compute differently).  data: DEVICE array
+ * of nblocks * 1024 uint32 words, updated in place (block b owns words
+ * [b*1024, (b+1)*1024), thread t of it the words q*256 + t, q = 0..3); the
+ * outer loop runs `iters` times, each path `rounds` compute rounds.
+ * variant: DARM_DIVERGENT or DARM_MELDED / DARM_AUTO.  Asynchronous on
+ * `stream`.  Errors: DARM_ERR_INVALID_ARG (pattern, negative counts, NULL
+ * data), DARM_ERR_CUDA. */
+int darm_sb_run(int pattern, uint32_t* data, size_t nblocks, int iters, int rounds, int variant,
+                void* stream);
+
 /* ---- melding analysis (host only) -------------------------------------- */
 
 /* One instruction of a divergent path: `opcode` is what the frequency

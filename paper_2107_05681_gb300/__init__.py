@@ -61,6 +61,7 @@ _sig = {
                                     _i32),
     "darm_oddeven_sort_block": ([_vp, _vp, _sz, _i32, _vp], _i32),
     "darm_oddeven_sort_buckets": ([_vp, _vp, _sz, _sz, _i32, _vp], _i32),
+    "darm_sb_run": ([_i32, _vp, _sz, _i32, _i32, _i32, _vp], _i32),
     "darm_meld_mp_block": ([_vp, _i32, _vp, _i32], ctypes.c_double),
     "darm_meld_mp_subgraph": ([_vp, _vp, _vp, _vp, _i32], ctypes.c_double),
     "darm_meld_align": ([_vp, _i32, _vp, _i32, ctypes.c_double, _vp, _vp], _i32),
@@ -177,6 +178,25 @@ def oddeven_sort_block(keys, vals=None, variant="melded", stream=None) -> None:
     rc = lib.darm_oddeven_sort_block(ctypes.c_void_p(keys.data_ptr()), vp, keys.numel(),
                                      _variant(variant), _stream_handle(stream))
     _check(rc, "darm_oddeven_sort_block")
+
+
+# ---- synthetic divergent kernels -----------------------------------------------
+
+SB_PATTERNS = {"SB1": 1, "SB4": 4, "SB1-R": 101, "SB4-R": 104}
+
+
+def sb_run(pattern: str, data, iters: int, rounds: int, variant="melded", stream=None) -> None:
+    """Run a synthetic divergent kernel (SB1, SB4, SB1-R, SB4-R) in place on a
+    contiguous uint32 CUDA tensor of whole 1024-word blocks."""
+    import torch
+    if data.dtype != torch.uint32 or not data.is_cuda or not data.is_contiguous():
+        raise ValueError("data must be a contiguous uint32 CUDA tensor")
+    if data.numel() % 1024:
+        raise ValueError("data must hold whole blocks of 1024 words")
+    rc = lib.darm_sb_run(SB_PATTERNS[pattern], ctypes.c_void_p(data.data_ptr()),
+                         data.numel() // 1024, int(iters), int(rounds), _variant(variant),
+                         _stream_handle(stream))
+    _check(rc, "darm_sb_run")
 
 
 # ---- melding analysis (host only) ----------------------------------------------

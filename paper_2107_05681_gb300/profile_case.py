@@ -6,6 +6,7 @@ profiler can capture the second sort's kernel launches.
 VARIANT: melded | divergent.  WORKLOAD: cfg1 (4096 uint32 keys, one block),
 oem4096 (the same keys through the single-block odd-even merge sort network),
 oem26 (2^26 uint32 keys through that network in buckets of 4096, one block each),
+SB1 | SB4 | SB1-R | SB4-R (the synthetic divergent kernels, 1216 blocks),
 kv24 (2^24 uint32 key-value pairs), f32 (2^26 float32 keys).
 """
 import sys
@@ -19,6 +20,14 @@ import synth
 
 def main(variant="melded", workload="kv24"):
     darm.init(0)
+    if workload.startswith("SB"):
+        data = torch.from_numpy(synth.uniform_u32(0xDA2C0007, 1024 * 152 * 8)).cuda()
+        for _ in range(2):
+            d2 = data.clone()
+            darm.sb_run(workload, d2, 16, 32, variant=variant)
+        torch.cuda.synchronize()
+        print("ok", darm.launch_count())
+        return
     if workload in ("oem4096", "oem26"):
         keys = synth.cfg1_keys() if workload == "oem4096" else synth.uniform_u32(0xDA2C0006, 1 << 26)
         K = torch.from_numpy(keys).cuda()
