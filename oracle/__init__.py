@@ -176,7 +176,8 @@ def oddeven_sort(keys, vals=None, recursive=False):
     return k, v, ncmp
 
 
-SB_PATTERNS = {"SB1": 1, "SB4": 4, "SB1-R": 101, "SB4-R": 104}
+SB_PATTERNS = {"SB1": 1, "SB2": 2, "SB3": 3, "SB4": 4,
+               "SB1-R": 101, "SB2-R": 102, "SB3-R": 103, "SB4-R": 104}
 
 
 def sb_run(pattern: str, data, iters: int, rounds: int):

@@ -24,7 +24,8 @@
  *     extreme key before the network runs.
  *   - oracle_oddeven_u32 / oracle_oddeven_rec_u32: Batcher's odd-even merge
  *     sort network (PCM's base, Section VI-A), iterative and recursive.
- *   - oracle_sb: the synthetic divergent kernels SB1, SB4, SB1-R, SB4-R.
+ *   - oracle_sb: the synthetic divergent kernels SB1-SB4 and their -R
+ *     variants.
  *
  * Readings of the paper taken here (the paper is silent on them):
  *   - descending order flips every comparator: the ascending test of Fig. 1
@@ -322,11 +323,19 @@ int oracle_oddeven_rec_u32(uint32_t* key, uint32_t* val, uint64_t n) {
  *       identical paths:  g(v, w) = 3v + w
  *       -R paths:         c = 0: 3v + w,  c = 1: 5v ^ w,  c = 2: 7v - w
  *   (all arithmetic modulo 2^32).
- * pattern: 1 SB1, 4 SB4, 101 SB1-R, 104 SB4-R.  Status 1 on a bad pattern.
+ *   SB2:  the SB1 paths, each holding an if-then region guarded by the
+ *         data: if (s[b] & 1) run the rounds (paired regions B2 / B3);
+ *   SB3:  the SB1 paths, each holding two if-then regions: the SB2 one,
+ *         then if (s[a] & 2) run rounds of s[b] = g2(s[b], s[a]) (paired
+ *         regions C2 / C3 and C6 / C5), g2 = 3v + w, or in SB3-R
+ *         path 0: 7v - w, path 1: 3v + w.
+ * pattern: 1 SB1, 2 SB2, 3 SB3, 4 SB4, 101..104 their -R variants.  Status 1
+ * on a bad pattern.
  */
 int oracle_sb(int pattern, uint32_t* data, uint64_t nblocks, int iters, int rounds) {
-  if (pattern != 1 && pattern != 4 && pattern != 101 && pattern != 104) return 1;
-  const int three_way = (pattern == 4 || pattern == 104);
+  const int base = pattern % 100;
+  if (base < 1 || base > 4 || (pattern != base && pattern != base + 100)) return 1;
+  const int three_way = (base == 4);
   const int same = (pattern < 100);
   for (uint64_t blk = 0; blk < nblocks; ++blk) {
     uint32_t* d = data + blk * 1024;
@@ -345,14 +354,24 @@ int oracle_sb(int pattern, uint32_t* data, uint64_t nblocks, int iters, int roun
             c = c ? 0u : 1u; /* path index: 0 = first path, 1 = second */
           }
           b = (a + 1) & 3u;
-          for (int r = 0; r < rounds; ++r) {
-            const uint32_t v = s[a], w = s[b];
-            if (same || c == 0)
-              s[a] = 3u * v + w;
-            else if (c == 1)
-              s[a] = (5u * v) ^ w;
-            else
-              s[a] = 7u * v - w;
+          if (base >= 2 && base <= 3 && (s[b] & 1u) == 0u) {
+            /* first region not taken */
+          } else {
+            for (int r = 0; r < rounds; ++r) {
+              const uint32_t v = s[a], w = s[b];
+              if (same || c == 0)
+                s[a] = 3u * v + w;
+              else if (c == 1)
+                s[a] = (5u * v) ^ w;
+              else
+                s[a] = 7u * v - w;
+            }
+          }
+          if (base == 3 && (s[a] & 2u) != 0u) {
+            for (int r = 0; r < rounds; ++r) {
+              const uint32_t v = s[b], w = s[a];
+              s[b] = (same || c == 1) ? 3u * v + w : 7u * v - w;
+            }
           }
         }
       }

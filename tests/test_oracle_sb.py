@@ -32,6 +32,22 @@ def test_hand_traces_one_iteration_one_round():
     assert _words_of_thread(oracle.sb_run("SB4-R", d, 1, 1), 1) == [1793, 1796, 6921, 5382]
 
 
+def test_hand_traces_if_then_regions():
+    d = np.arange(1024, dtype=np.uint32)
+    # SB2, thread 1 (s = 1, 257, 513, 769): j=0 path 0, s1 odd -> s0=3*1+257=260;
+    # j=1 path 1 (a=3, b=0), s0=260 even -> skip; j=2 path 0, s3 odd ->
+    # s2=3*513+769=2308; j=3 path 1 (a=1, b=2), s2 even -> skip
+    assert _words_of_thread(oracle.sb_run("SB2", d, 1, 1), 1) == [260, 257, 2308, 769]
+    # SB3, thread 2 (s = 2, 258, 514, 770): j=0 path 1 (a=2, b=3): s3 even;
+    # s2&2 -> s3=3*770+514=2824.  j=1 path 0 (a=1, b=2): s2 even; s1&2 ->
+    # s2=3*514+258=1800.  j=2 path 1 (a=0, b=1): s1 even; s0&2 ->
+    # s1=3*258+2=776.  j=3 path 0 (a=3, b=0): s0 even; s3&2 == 0
+    assert _words_of_thread(oracle.sb_run("SB3", d, 1, 1), 2) == [2, 776, 1800, 2824]
+    # SB3-R, thread 2: as SB3 but path 0's second region is 7v - w:
+    # j=1 -> s2=7*514-258=3340
+    assert _words_of_thread(oracle.sb_run("SB3-R", d, 1, 1), 2) == [2, 776, 3340, 2824]
+
+
 def test_blocks_are_independent():
     rng = np.random.default_rng(9)
     d = rng.integers(0, 2**32, 4096, dtype=np.uint64).astype(np.uint32)
@@ -46,6 +62,8 @@ def test_identical_and_random_variants_differ():
     d = rng.integers(0, 2**32, 1024, dtype=np.uint64).astype(np.uint32)
     assert not np.array_equal(oracle.sb_run("SB1", d, 2, 2), oracle.sb_run("SB1-R", d, 2, 2))
     assert not np.array_equal(oracle.sb_run("SB4", d, 2, 2), oracle.sb_run("SB4-R", d, 2, 2))
+    assert not np.array_equal(oracle.sb_run("SB2", d, 2, 2), oracle.sb_run("SB2-R", d, 2, 2))
+    assert not np.array_equal(oracle.sb_run("SB3", d, 2, 2), oracle.sb_run("SB3-R", d, 2, 2))
 
 
 def test_rejects_bad_input():
