@@ -187,8 +187,10 @@ int darm_oddeven_sort_buckets(uint32_t* keys, uint32_t* vals, size_t n, size_t b
 /* The paper's synthetic kernels, as built here: two nested loops whose inner
  * loop holds a divergent region; each path works on different words of the
  * thread's shared-memory slice.  pattern: 1 = SB1 (two-way diamond, paths
- * compute identically), 4 = SB4 (three-way if-else-if-else, identical),
- * 101 = SB1-R, 104 = SB4-R (paths compute differently).  data: DEVICE array
+ * compute identically), 2 = SB2 (each path an if-then region guarded by the
+ * data), 3 = SB3 (two such regions per path), 4 = SB4 (three-way
+ * if-else-if-else); 101..104 = their -R variants (paths compute
+ * differently).  data: DEVICE array
  * of nblocks * 1024 uint32 words, updated in place (block b owns words
  * [b*1024, (b+1)*1024), thread t of it the words q*256 + t, q = 0..3); the
  * outer loop runs `iters` times, each path `rounds` compute rounds.

@@ -182,11 +182,12 @@ def oddeven_sort_block(keys, vals=None, variant="melded", stream=None) -> None:
 
 # ---- synthetic divergent kernels -----------------------------------------------
 
-SB_PATTERNS = {"SB1": 1, "SB4": 4, "SB1-R": 101, "SB4-R": 104}
+SB_PATTERNS = {"SB1": 1, "SB2": 2, "SB3": 3, "SB4": 4,
+               "SB1-R": 101, "SB2-R": 102, "SB3-R": 103, "SB4-R": 104}
 
 
 def sb_run(pattern: str, data, iters: int, rounds: int, variant="melded", stream=None) -> None:
-    """Run a synthetic divergent kernel (SB1, SB4, SB1-R, SB4-R) in place on a
+    """Run a synthetic divergent kernel (SB1-SB4, SB1-R-SB4-R) in place on a
     contiguous uint32 CUDA tensor of whole 1024-word blocks."""
     import torch
     if data.dtype != torch.uint32 or not data.is_cuda or not data.is_contiguous():

@@ -1,5 +1,5 @@
-// synthetic.cu - the paper's synthetic divergent kernels SB1 and SB4 and
-// their -R variants (Section VI-A), in a divergent and a melded form.
+// synthetic.cu - the paper's synthetic divergent kernels SB1-SB4 and their
+// -R variants (Section VI-A), in a divergent and a melded form.
 //
 // Two nested loops; the inner loop holds a divergent region whose paths work
 // on different words of the thread's shared-memory slice.  SB1: a two-way
@@ -13,7 +13,13 @@
 // (word indices mod 4); the path then runs `rounds` times
 //   v = g_path(v, w),  g_0 = 3v + w,  g_1 = 5v ^ w,  g_2 = 7v - w  (-R)
 //   v = 3v + w                                                      (SB1, SB4)
-// on v = s[a], w = s[b] and stores v back to s[a].  The path condition
+// on v = s[a], w = s[b] and stores v back to s[a].
+//   SB2:  the SB1 paths, each an if-then region guarded by the data
+//         (s[b] & 1) around the rounds (paired regions B2 / B3);
+//   SB3:  the SB1 paths with two if-then regions each: the SB2 one, then,
+//         if (s[a] & 2), rounds of s[b] = g2(s[b], s[a]) (regions C2 / C3
+//         and C6 / C5), g2 = 3v + w, or in SB3-R path 0: 7v - w.
+// The path condition
 // alternates between neighbouring lanes, so every warp takes every path.
 //
 // Divergent form: one branch per path with its own loads, loop and store.
@@ -51,9 +57,32 @@ __device__ __forceinline__ void sb_path(uint32_t* s, uint32_t t, uint32_t a, uin
   s[a * kSbThreads + t] = v;
 }
 
+// SB2 / SB3: the path's if-then regions (divergent form)
+template <int PATH, bool SAME, bool TWO_REGIONS>
+__device__ __forceinline__ void sb_regions(uint32_t* s, uint32_t t, uint32_t a, uint32_t b,
+                                           int rounds) {
+  const uint32_t w = s[b * kSbThreads + t];
+  if (w & 1u) {  // region B2 / B3 (C2 / C3)
+    uint32_t v = s[a * kSbThreads + t];
+    for (int r = 0; r < rounds; ++r) v = sb_round<PATH, SAME>(v, w);
+    s[a * kSbThreads + t] = v;
+  }
+  if (TWO_REGIONS) {
+    const uint32_t x = s[a * kSbThreads + t];
+    if (x & 2u) {  // region C6 / C5
+      uint32_t u = s[b * kSbThreads + t];
+      for (int r = 0; r < rounds; ++r) u = (SAME || PATH == 1) ? 3u * u + x : 7u * u - x;
+      s[b * kSbThreads + t] = u;
+    }
+  }
+}
+
 template <int PATTERN, int VAR>
 __global__ void __launch_bounds__(kSbThreads) darm_sb_kernel(uint32_t* data, int iters, int rounds) {
-  constexpr bool THREE = (PATTERN == 4 || PATTERN == 104);
+  constexpr int BASE = PATTERN % 100;
+  constexpr bool THREE = (BASE == 4);
+  constexpr bool REGIONS = (BASE == 2 || BASE == 3);
+  constexpr bool TWO_REGIONS = (BASE == 3);
   constexpr bool SAME = (PATTERN < 100);
   __shared__ uint32_t s[4 * kSbThreads];
   const uint32_t t = threadIdx.x;
@@ -69,7 +98,49 @@ __global__ void __launch_bounds__(kSbThreads) darm_sb_kernel(uint32_t* data, int
       } else {
         c = ((t ^ j ^ uint32_t(it)) & 1u) ? 0u : 1u;
       }
-      if (VAR == 0) {
+      if (REGIONS) {
+        if (VAR == 0) {
+          if (c == 0)
+            sb_regions<0, SAME, TWO_REGIONS>(s, t, j & 3u, (j + 1) & 3u, rounds);
+          else
+            sb_regions<1, SAME, TWO_REGIONS>(s, t, (j + 2) & 3u, (j + 3) & 3u, rounds);
+        } else {
+          // the paths' regions melded pairwise: selected words and, in the
+          // -R variants, selected multipliers and operations
+          const uint32_t a = c == 0 ? (j & 3u) : ((j + 2) & 3u);
+          const uint32_t b = (a + 1) & 3u;
+          const uint32_t w = s[b * kSbThreads + t];
+          if (w & 1u) {
+            uint32_t v = s[a * kSbThreads + t];
+            if (SAME) {
+              for (int r = 0; r < rounds; ++r) v = 3u * v + w;
+            } else {
+              const uint32_t mul = c == 0 ? 3u : 5u;
+              for (int r = 0; r < rounds; ++r) {
+                const uint32_t m = mul * v;
+                v = c == 0 ? m + w : m ^ w;
+              }
+            }
+            s[a * kSbThreads + t] = v;
+          }
+          if (TWO_REGIONS) {
+            const uint32_t x = s[a * kSbThreads + t];
+            if (x & 2u) {
+              uint32_t u = s[b * kSbThreads + t];
+              if (SAME) {
+                for (int r = 0; r < rounds; ++r) u = 3u * u + x;
+              } else {
+                const uint32_t mul = c == 0 ? 7u : 3u;
+                for (int r = 0; r < rounds; ++r) {
+                  const uint32_t m = mul * u;
+                  u = c == 0 ? m - x : m + x;
+                }
+              }
+              s[b * kSbThreads + t] = u;
+            }
+          }
+        }
+      } else if (VAR == 0) {
         if (THREE) {
           if (c == 0)
             sb_path<0, SAME>(s, t, j & 3u, (j + 1) & 3u, rounds);
@@ -125,7 +196,8 @@ extern "C" int darm_sb_run(int pattern, uint32_t* data, size_t nblocks, int iter
                            int variant, void* stream) {
   if (!g_ctx.inited) return DARM_ERR_NOT_INIT;
   if (variant < DARM_DIVERGENT || variant > DARM_AUTO) return DARM_ERR_INVALID_ARG;
-  if (pattern != 1 && pattern != 4 && pattern != 101 && pattern != 104) return DARM_ERR_INVALID_ARG;
+  const int base = pattern % 100;
+  if (base < 1 || base > 4 || (pattern != base && pattern != base + 100)) return DARM_ERR_INVALID_ARG;
   if (iters < 0 || rounds < 0 || nblocks > size_t(0x7FFFFFFF)) return DARM_ERR_INVALID_ARG;
   if (nblocks == 0) return DARM_OK;
   if (!data) return DARM_ERR_INVALID_ARG;
@@ -134,8 +206,12 @@ extern "C" int darm_sb_run(int pattern, uint32_t* data, size_t nblocks, int iter
   const uint32_t nb = uint32_t(nblocks);
   switch (pattern) {
     case 1: sb_launch<1>(melded, data, nb, iters, rounds, s); break;
+    case 2: sb_launch<2>(melded, data, nb, iters, rounds, s); break;
+    case 3: sb_launch<3>(melded, data, nb, iters, rounds, s); break;
     case 4: sb_launch<4>(melded, data, nb, iters, rounds, s); break;
     case 101: sb_launch<101>(melded, data, nb, iters, rounds, s); break;
+    case 102: sb_launch<102>(melded, data, nb, iters, rounds, s); break;
+    case 103: sb_launch<103>(melded, data, nb, iters, rounds, s); break;
     default: sb_launch<104>(melded, data, nb, iters, rounds, s); break;
   }
   if (cudaGetLastError() != cudaSuccess) return DARM_ERR_CUDA;

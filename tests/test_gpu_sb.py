@@ -11,7 +11,8 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("variant", ["divergent", "melded"])
-@pytest.mark.parametrize("pattern", ["SB1", "SB4", "SB1-R", "SB4-R"])
+@pytest.mark.parametrize("pattern", ["SB1", "SB2", "SB3", "SB4", "SB1-R", "SB2-R", "SB3-R",
+                                     "SB4-R"])
 @pytest.mark.parametrize("iters,rounds", [(0, 3), (1, 1), (3, 5), (7, 16)])
 def test_matches_oracle(darm, pattern, variant, iters, rounds):
     import torch
