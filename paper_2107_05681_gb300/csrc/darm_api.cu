@@ -41,7 +41,8 @@ int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_
     P.vals = vals;
     P.status = g_ctx.d_status;
     const void* fn =
-        L.win2 ? ((kk == KEY_U32) ? window2_kernel_u32(has_vals, L.loge, int(L.P.c), L.variant)
+        L.win1 ? window1_kernel(kk == KEY_U64, has_vals, L.loge, int(L.P.c)).fn
+        : L.win2 ? ((kk == KEY_U32) ? window2_kernel_u32(has_vals, L.loge, int(L.P.c), L.variant)
                                   : window2_kernel_u64(has_vals, L.loge, int(L.P.c), L.variant)).fn
         : L.tma ? tma_merge_kernel_u32(has_vals, L.loge, int(L.P.b), L.tma, L.variant, nullptr).fn
         : L.fixed ? fixed_kernel_fn(kk, has_vals, L.loge, int(L.P.b), L.variant, L.kind == PASS_MERGE)

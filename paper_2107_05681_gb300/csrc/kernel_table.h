@@ -29,6 +29,9 @@ KernelEntry tma_merge_kernel_u32(bool has_vals, int loge, int logt, int ns, int 
 // Two-window passes with a compile-time shape (window2_kernel.cuh): E =
 // 2^loge, c low consecutive-element bits.
 KernelEntry window2_kernel_u32(bool has_vals, int loge, int c, int var);
+// One-window passes with a compile-time shape (window1_kernel.cuh): 2^c
+// threads, E = 2^loge; nullptr where none was built.
+KernelEntry window1_kernel(bool u64, bool has_vals, int loge, int c);
 KernelEntry window2_kernel_u64(bool has_vals, int loge, int c, int var);
 
 // Call fn(kernel address, ctx) for every instantiation (used to configure

@@ -253,6 +253,8 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
         r.dst = LOC_GLOBAL;
         r.lanediv = 0;  // bit p lies above the window: one direction per block
         set_rounds(L.P, std::vector<Round>{r});
+        const KernelEntry w1e = window1_kernel(kk == KEY_U64, has_vals, e2, c);
+        L.win1 = w1e.fn != nullptr && int(L.threads) == w1e.max_threads;
       } else {
         const int sbits = nr * e2;
         const int w0 = hi - sbits + 1;

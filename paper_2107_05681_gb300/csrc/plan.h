@@ -47,6 +47,7 @@ struct Launch {
   int tma;     // persistent merge with bulk-copy prefetch into this many
                // staging buffers (tma_merge.cuh); 0: plain merge kernel
   bool win2;   // two-window pass with a compile-time shape (window2_kernel.cuh)
+  bool win1;   // one-window pass with a compile-time shape (window1_kernel.cuh)
   int loge;
   int variant;
   uint32_t grid;

@@ -1,5 +1,6 @@
-// window2.cu - instantiations of the two-window pass kernel.
+// window2.cu - instantiations of the one- and two-window pass kernels.
 #include "kernel_table.h"
+#include "window1_kernel.cuh"
 #include "window2_kernel.cuh"
 
 namespace darm {
@@ -13,7 +14,23 @@ KernelEntry wentry(int var) {
   return KernelEntry{reinterpret_cast<const void*>(&darm_window2_kernel<K, V, LOGE, C, 0, MT>), MT};
 }
 
+template <typename K, bool V, int LOGE, int C>
+KernelEntry w1entry() {
+  constexpr int MT = 1 << C;
+  return KernelEntry{reinterpret_cast<const void*>(&darm_window1_kernel<K, V, LOGE, C, MT>), MT};
+}
+
 }  // namespace
+
+KernelEntry window1_kernel(bool u64, bool has_vals, int loge, int c) {
+  if (c != 8) return KernelEntry{nullptr, 0};
+  if (!u64 && has_vals && loge == 4) return w1entry<uint32_t, true, 4, 8>();
+  if (!u64 && !has_vals && loge == 5) return w1entry<uint32_t, false, 5, 8>();
+  if (!u64 && !has_vals && loge == 4) return w1entry<uint32_t, false, 4, 8>();
+  if (u64 && has_vals && loge == 3) return w1entry<uint64_t, true, 3, 8>();
+  if (u64 && !has_vals && loge == 4) return w1entry<uint64_t, false, 4, 8>();
+  return KernelEntry{nullptr, 0};
+}
 
 KernelEntry window2_kernel_u32(bool has_vals, int loge, int c, int var) {
   if (has_vals && loge == 4 && c == 4) return wentry<uint32_t, true, 4, 4>(var);
