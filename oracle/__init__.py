@@ -150,7 +150,7 @@ def segmented_sort(keys, vals, offsets, lengths, desc=False, desc_per_seg=None,
     return k, v
 
 
-def oddeven_sort(keys, vals=None, recursive=False):
+def oddeven_sort(keys, vals=None, recursive=False, mutant=0):
     """Sort copies of uint32 ``keys`` (and ``vals``) with Batcher's odd-even
     merge sort network (ascending).  Returns (keys_out, vals_out or None,
     comparators evaluated, or None for the recursive form)."""
@@ -163,11 +163,11 @@ def oddeven_sort(keys, vals=None, recursive=False):
         if v.shape != k.shape:
             raise ValueError("vals must match keys")
     if recursive:
-        rc = _lib().oracle_oddeven_rec_u32(_ptr(k), _ptr(v), k.size)
+        rc = _lib(mutant).oracle_oddeven_rec_u32(_ptr(k), _ptr(v), k.size)
         ncmp = None
     else:
         c = ctypes.c_uint64(0)
-        rc = _lib().oracle_oddeven_u32(_ptr(k), _ptr(v), k.size, ctypes.byref(c))
+        rc = _lib(mutant).oracle_oddeven_u32(_ptr(k), _ptr(v), k.size, ctypes.byref(c))
         ncmp = int(c.value)
     if rc == ERR_NOT_POW2:
         raise ValueError("length must be a power of two")

@@ -240,8 +240,10 @@ int oracle_mutant_id(void) { return DARM_ORACLE_MUTANT; }
  * statement of the network (Knuth, TAOCP vol. 3, 5.3.4).
  * `ncmp` (nullable) receives the number of comparators evaluated.
  */
+/* DARM_ORACLE_MUTANT 6 drops the same-block test of the iterative form,
+ * 7 swaps equal keys too (non-strict compare); 0 in every real build. */
 static void oe_cmpx(uint32_t* key, uint32_t* val, uint64_t a, uint64_t b) {
-  if (key[b] < key[a]) {
+  if (DARM_ORACLE_MUTANT == 7 ? (key[b] <= key[a]) : (key[b] < key[a])) {
     uint32_t tk = key[a];
     key[a] = key[b];
     key[b] = tk;
@@ -261,7 +263,7 @@ int oracle_oddeven_u32(uint32_t* key, uint32_t* val, uint64_t n, uint64_t* ncmp)
       for (uint64_t j = k % p; j + k < n; j += 2 * k) {
         for (uint64_t i = 0; i < k && i + j + k < n; ++i) {
           const uint64_t x = i + j;
-          if (x / (2 * p) == (x + k) / (2 * p)) {
+          if (DARM_ORACLE_MUTANT == 6 || x / (2 * p) == (x + k) / (2 * p)) {
             oe_cmpx(key, val, x, x + k);
             ++count;
           }

@@ -76,3 +76,33 @@ def test_small_hand_case():
 def test_rejects_non_power_of_two():
     with pytest.raises(ValueError):
         oracle.oddeven_sort(np.arange(6, dtype=np.uint32))
+
+
+def _pins_fail(mutant):
+    """True when some pin of this file rejects an oracle built with a planted
+    mistake (run on small cases)."""
+    fails = []
+    # comparator count
+    for p in range(2, 7):
+        _, _, ncmp = oracle.oddeven_sort(np.zeros(1 << p, np.uint32), mutant=mutant)
+        if ncmp != (p * p - p + 4) * (1 << (p - 2)) - 1:
+            fails.append("count")
+            break
+    # equal keys never move / payload order equals the recursive form
+    for m in (3, 6):
+        n = 1 << m
+        keys = synth.uniform_u32(610 + m, n) % np.uint32(3)
+        vals = np.arange(n, dtype=np.uint32)
+        k1, v1, _ = oracle.oddeven_sort(keys, vals, mutant=mutant)
+        k2, v2, _ = oracle.oddeven_sort(keys, vals, recursive=True)  # the real build
+        if not (np.array_equal(k1, k2) and np.array_equal(v1, v2)):
+            fails.append("recursive")
+            break
+    return fails
+
+
+@pytest.mark.parametrize("mutant", [6, 7])
+def test_pins_catch_planted_mistakes(mutant):
+    """6: the same-block test dropped; 7: equal keys swapped."""
+    assert _pins_fail(mutant), f"mutant {mutant} passed every odd-even pin"
+    assert not _pins_fail(0)
