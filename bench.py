@@ -2,9 +2,11 @@
 """Benchmark: sorted keys/s of the bitonic network, melded vs divergent kernels.
 
 One step = one whole sort (every pass of the network) of one synthetic array
-already resident in HBM.  Default workload: key-value sort of 2^24 uniform
-uint32 keys with a uint32 payload (payload = index).  `--workload f32` runs
-2^26 float32 keys (N(0,1) with duplicates and signed zeros).
+already resident in HBM.  Default workload: 2^26 float32 keys (N(0,1) with 1 %
+exact duplicates and signed zeros, ordered by the IEEE-754 totalOrder bit
+map), the paper's 2^26-element bitonic input.  `--workload kv24` runs the
+key-value sort of 2^24 uniform uint32 keys with a uint32 payload (payload =
+index).
 
 Prints ONE JSON line on rank 0.  Under torchrun (N > 1) every rank sorts its
 own replica (the network of one array does not shard without an exchange
@@ -40,7 +42,7 @@ def parse_args():
     ap.add_argument("--workload",
                     choices=["kv24", "kv24skew", "f32", "cfg1", "oem4096", "oem26", "sb",
                              "seg", "serve"],
-                    default="kv24")
+                    default="f32")
     ap.add_argument("--serve-requests", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -1,7 +1,7 @@
 """Run one workload's sort twice (a warm-up and the captured one) so that a
 profiler can capture the second sort's kernel launches.
 
-    python -m paper_2107_05681_gb300.profile_case VARIANT WORKLOAD
+    python profile_case.py VARIANT WORKLOAD
 
 VARIANT: melded | divergent.  WORKLOAD: cfg1 (4096 uint32 keys, one block),
 oem4096 (the same keys through the single-block odd-even merge sort network),
