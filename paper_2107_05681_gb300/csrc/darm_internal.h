@@ -58,7 +58,8 @@ int segmented_parse(const uint64_t* seg_offsets, const uint32_t* seg_len, uint32
 
 // Capacity-1 segments: write the sentinel into the empty ones.  base[i] is
 // the element offset, len_desc[i] bit 0 = real length 1, bit 1 = descending.
-void launch_singletons(uint32_t* keys, uint32_t* vals, const uint64_t* base,
-                       const uint32_t* len_desc, uint32_t n, cudaStream_t s);
+// Returns the status of this launch alone.
+cudaError_t launch_singletons(uint32_t* keys, uint32_t* vals, const uint64_t* base,
+                              const uint32_t* len_desc, uint32_t n, cudaStream_t s);
 
 }  // namespace darm

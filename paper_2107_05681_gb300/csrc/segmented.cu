@@ -53,10 +53,13 @@ __global__ void seg_singletons_kernel(uint32_t* keys, uint32_t* vals, const uint
 
 }  // namespace
 
-void launch_singletons(uint32_t* keys, uint32_t* vals, const uint64_t* base,
-                       const uint32_t* len_desc, uint32_t n, cudaStream_t s) {
-  if (n == 0) return;
-  seg_singletons_kernel<<<(n + 255) / 256, 256, 0, s>>>(keys, vals, base, len_desc, n);
+cudaError_t launch_singletons(uint32_t* keys, uint32_t* vals, const uint64_t* base,
+                              const uint32_t* len_desc, uint32_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  void* args[] = {&keys, &vals, &base, &len_desc, &n};
+  // the status of this launch alone (no sticky error of earlier work)
+  return cudaLaunchKernel(reinterpret_cast<const void*>(&seg_singletons_kernel),
+                          dim3((n + 255) / 256), dim3(256), args, 0, s);
 }
 
 namespace {
@@ -148,7 +151,9 @@ int build_seg_plan(SegPlan& sp, uint32_t* keys, uint32_t* vals, const std::vecto
   cudaMemsetAsync(sp.d_counter, 0, ncounters * sizeof(unsigned int), cs);
   rc = launch_plan(sp.launches, kk, keys, vals, cs, /*count=*/false);
   if (rc == DARM_OK && sp.n_single) {
-    launch_singletons(keys, vals, sp.d_single_base, sp.d_single_ld, sp.n_single, cs);
+    if (launch_singletons(keys, vals, sp.d_single_base, sp.d_single_ld, sp.n_single, cs) !=
+        cudaSuccess)
+      rc = DARM_ERR_CUDA;
   }
   cudaGraph_t graph = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(cs, &graph);

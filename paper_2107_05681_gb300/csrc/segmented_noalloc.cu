@@ -13,7 +13,9 @@
 // The array lives in every GPU that loads the library, for the life of the
 // process.  All calls share it and it keeps the last call's contents, so two
 // calls whose work overlaps on the GPU (different streams, or different host
-// threads) race on it; calls on one stream are ordered and safe.
+// threads) race on it; calls on one stream are ordered and safe.  The
+// tables are copied from host memory the call reuses and frees, so the call
+// refuses a stream that is capturing a graph (DARM_ERR_INVALID_ARG).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -75,6 +77,16 @@ extern "C" int darm_segmented_sort_noalloc(uint32_t* keys, uint32_t* vals,
   if (!keys || !seg_offsets || !seg_len) return DARM_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(keys) & 15u) != 0) return DARM_ERR_INVALID_ARG;
   if (vals && (reinterpret_cast<uintptr_t>(vals) & 15u) != 0) return DARM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // Each launch's tables are copied from host memory that this call reuses
+  // and frees, so a graph captured from this call would replay copies of
+  // freed memory: refuse a capturing stream before enqueueing anything.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    fprintf(stderr, "darm_segmented_sort_noalloc: the stream is capturing a graph; call it "
+                    "outside stream capture\n");
+    return DARM_ERR_INVALID_ARG;
+  }
   std::vector<BatchSeg> segs;
   int rc = segmented_parse(seg_offsets, seg_len, num_segs, dir, seg_desc, segs);
   if (rc != DARM_OK) return rc;
@@ -87,7 +99,7 @@ extern "C" int darm_segmented_sort_noalloc(uint32_t* keys, uint32_t* vals,
 
   const bool has_vals = vals != nullptr;
   int cmax = 0;
-  for (const BatchSeg& s : segs) cmax = std::max(cmax, s.c);
+  for (const BatchSeg& sg : segs) cmax = std::max(cmax, sg.c);
   const Tuning tn = batch_tuning(KEY_U32, has_vals, cmax);
   BatchTables bt;
   rc = batch_append(bt, KEY_U32, has_vals, tn, variant, segs, 0, 0);
@@ -98,10 +110,10 @@ extern "C" int darm_segmented_sort_noalloc(uint32_t* keys, uint32_t* vals,
   // singletons (capacity 1): their table goes through the scratch too
   std::vector<uint64_t> sbase;
   std::vector<uint32_t> sld;
-  for (const BatchSeg& s : segs)
-    if (s.c == 0) {
-      sbase.push_back(s.base);
-      sld.push_back((s.len ? 1u : 0u) | (s.desc ? 2u : 0u));
+  for (const BatchSeg& sg : segs)
+    if (sg.c == 0) {
+      sbase.push_back(sg.base);
+      sld.push_back((sg.len ? 1u : 0u) | (sg.desc ? 2u : 0u));
     }
 
   // Check every launch fits before enqueueing anything.
@@ -134,7 +146,6 @@ extern "C" int darm_segmented_sort_noalloc(uint32_t* keys, uint32_t* vals,
     return DARM_ERR_INVALID_ARG;
   }
 
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<unsigned char> staging;
   for (size_t i = 0; i < L; ++i) {
     // layout in the scratch: [counter (zeroed) | slots | blocks]
@@ -170,9 +181,10 @@ extern "C" int darm_segmented_sort_noalloc(uint32_t* keys, uint32_t* vals,
     if (cudaMemcpyAsync(base, staging.data(), staging.size(), cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
       return DARM_ERR_CUDA;
-    launch_singletons(keys, vals, reinterpret_cast<const uint64_t*>(base),
-                      reinterpret_cast<const uint32_t*>(base + off_ld), uint32_t(sbase.size()), s);
-    if (cudaGetLastError() != cudaSuccess) return DARM_ERR_CUDA;
+    if (launch_singletons(keys, vals, reinterpret_cast<const uint64_t*>(base),
+                          reinterpret_cast<const uint32_t*>(base + off_ld), uint32_t(sbase.size()),
+                          s) != cudaSuccess)
+      return DARM_ERR_CUDA;
     g_ctx.launches.fetch_add(1, std::memory_order_relaxed);
   }
   return DARM_OK;

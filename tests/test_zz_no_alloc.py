@@ -67,6 +67,62 @@ def test_noalloc_matches_allocating_entry_point_twice(darm, variant):
     assert darm.device_status() == darm.OK
 
 
+def test_noalloc_allocates_no_device_memory(darm):
+    """A warm call changes neither the device's free memory nor torch's
+    allocator: the tables go through the library's fixed array."""
+    import torch
+    segs = synth.cfg4_segments(seed=53, num_segments=300, min_len=1, max_len=20000,
+                               largest_first=True)
+    src_k, src_v = to_dev(segs.keys), to_dev(segs.vals)
+    k, v = src_k.clone(), src_v.clone()
+    _call_noalloc(darm, k, v, segs, "melded", None)  # first call: one-time set-up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        k.copy_(src_k)
+        v.copy_(src_v)
+        torch.cuda.synchronize()
+        before = torch.cuda.mem_get_info()[0]
+        _call_noalloc(darm, k, v, segs, "melded", None)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == before
+    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
+def test_noalloc_refuses_a_capturing_stream(darm):
+    """The call copies its tables from host memory it frees before returning,
+    so it must never be recorded into a CUDA graph: on a capturing stream it
+    returns DARM_ERR_INVALID_ARG and enqueues nothing."""
+    import torch
+    segs = synth.cfg4_segments(seed=54, num_segments=50, min_len=1, max_len=5000,
+                               largest_first=True)
+    k = to_dev(segs.keys)
+    off = np.ascontiguousarray(segs.offsets, dtype=np.uint64)
+    ln = np.ascontiguousarray(segs.lengths, dtype=np.uint32)
+    side = torch.cuda.Stream()
+    node = torch.zeros(16, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        g.capture_begin()
+        rc = darm.lib.darm_segmented_sort_noalloc(
+            ctypes.c_void_p(k.data_ptr()), None, off.ctypes.data_as(ctypes.c_void_p),
+            ln.ctypes.data_as(ctypes.c_void_p), ln.size, darm.ASC, darm.MELDED, None,
+            ctypes.c_void_p(side.cuda_stream))
+        node.add_(1.0)  # the capture holds one node of torch's own
+        g.capture_end()
+    assert rc == darm.ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    # nothing was enqueued: the keys are untouched
+    assert np.array_equal(k.cpu().numpy(), segs.keys)
+    # the same call outside the capture is valid and sorts
+    _call_noalloc(darm, k, None, segs, "melded", None)
+    torch.cuda.synchronize()
+    assert not np.array_equal(k.cpu().numpy(), segs.keys)
+
+
 def test_noalloc_rejects_layouts_beyond_its_scratch(darm):
     # 100,000 segments of capacity 32 in one tile pass: their slots alone
     # (16 bytes each) exceed the 1 MiB scratch
