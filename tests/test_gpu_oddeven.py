@@ -52,23 +52,66 @@ def test_rejects_bad_sizes(darm):
     assert k.cpu().numpy().tolist() == [5]
 
 
+_BUCKET_CACHE = {}
+
+
+def _oracle_buckets(keys, vals, bucket, tag):
+    """Every bucket sorted on its own by the oracle network (computed once
+    per input and shared by both kernel forms)."""
+    if tag not in _BUCKET_CACHE:
+        ek = np.empty_like(keys)
+        ev = None if vals is None else np.empty_like(vals)
+        for b in range(0, keys.size, bucket):
+            bk, bv, _ = oracle.oddeven_sort(keys[b:b + bucket],
+                                            None if vals is None else vals[b:b + bucket])
+            ek[b:b + bucket] = bk
+            if vals is not None:
+                ev[b:b + bucket] = bv
+        _BUCKET_CACHE.clear()
+        _BUCKET_CACHE[tag] = (ek, ev)
+    return _BUCKET_CACHE[tag]
+
+
+def _first_bad_bucket(got, exp, bucket):
+    bad = np.nonzero((got != exp).reshape(-1, bucket).any(axis=1))[0]
+    return None if bad.size == 0 else int(bad[0])
+
+
 @pytest.mark.parametrize("variant", ["divergent", "melded"])
 @pytest.mark.parametrize("bucket", [2, 256, 4096])
 def test_buckets_each_sorted_like_the_oracle(darm, bucket, variant):
-    """One thread block per bucket: every bucket equals the oracle's sort of
-    that bucket alone, payload order included."""
+    """One thread block per bucket: every bucket (all of them) equals the
+    oracle's sort of that bucket alone, payload order included."""
     import torch
     n = 1 << 18
     keys = synth.uniform_u32(800 + bucket, n) % np.uint32(512)
     vals = np.arange(n, dtype=np.uint32)
+    ek, ev = _oracle_buckets(keys, vals, bucket, ("ties", bucket))
     k, v = to_dev(keys), to_dev(vals)
     darm.oddeven_sort_buckets(k, v, bucket=bucket, variant=variant)
     torch.cuda.synchronize()
     gk, gv = k.cpu().numpy(), v.cpu().numpy()
-    for b in range(0, n, max(bucket, n // 64)):  # a spread of buckets
-        ek, ev, _ = oracle.oddeven_sort(keys[b:b + bucket], vals[b:b + bucket])
-        assert_equal(f"keys of bucket at {b}", gk[b:b + bucket], ek)
-        assert_equal(f"payload of bucket at {b}", gv[b:b + bucket], ev)
+    assert _first_bad_bucket(gk, ek, bucket) is None, "keys differ in a bucket"
+    assert _first_bad_bucket(gv, ev, bucket) is None, "payload differs in a bucket"
+    assert_equal("keys", gk, ek)
+    assert_equal("payload", gv, ev)
+
+
+@pytest.mark.parametrize("variant", ["divergent", "melded"])
+def test_oem26_full_size_every_bucket(darm, variant):
+    """The bucketed odd-even workload at full size, as the benchmark runs it:
+    2^26 uniform uint32 keys, 4096-key buckets, one thread block each; all
+    16,384 buckets against the oracle."""
+    import torch
+    bucket = 4096
+    keys = synth.uniform_u32(0xDA2C0006, 1 << 26)
+    ek, _ = _oracle_buckets(keys, None, bucket, ("oem26", bucket))
+    k = to_dev(keys)
+    darm.oddeven_sort_buckets(k, bucket=bucket, variant=variant)
+    torch.cuda.synchronize()
+    gk = k.cpu().numpy()
+    bad = _first_bad_bucket(gk, ek, bucket)
+    assert bad is None, f"bucket {bad} differs from the oracle"
 
 
 def test_bucket_arguments_are_checked(darm):

@@ -65,6 +65,52 @@ def test_mixed_equals_alone_and_oracle(server):
     assert 0 < p50 <= p99 and kps > 0
 
 
+_FULL_RANGE = {}
+
+
+def _full_range_requests():
+    """Requests over the whole serving size range, 2^8 .. 2^20 keys (uint64
+    keys, uint32 payload = index, mixed directions), both ends included, with
+    the oracle's results computed once and shared by both kernel forms."""
+    if not _FULL_RANGE:
+        reqs = synth.cfg5_requests(seed=0xDA2C0005, count=30, materialize=True)
+        for n, desc, seed in ((1 << 20, False, 61), (1 << 20, True, 62), (256, True, 63),
+                              ((1 << 20) - 3, True, 64), (257, False, 65)):
+            reqs.append(synth.Request(0.0, n, desc, synth.uniform_u64(seed, n),
+                                      np.arange(n, dtype=np.uint32)))
+        _FULL_RANGE["reqs"] = reqs
+        _FULL_RANGE["expected"] = [_expected(r) for r in reqs]
+    return _FULL_RANGE["reqs"], _FULL_RANGE["expected"]
+
+
+@pytest.mark.parametrize("variant", ["melded", "divergent"])
+def test_full_size_range_alone_and_mixed_equal_the_oracle(darm, variant):
+    """Every request of 2^8 .. 2^20 keys equals the oracle's sort, alone on
+    the GPU and admitted into a mix under a budget that holds only part of
+    the batch at once (so later requests join while others run)."""
+    import torch
+    reqs, expected = _full_range_requests()
+    assert min(r.n for r in reqs) == 256 and max(r.n for r in reqs) == 1 << 20
+    darm.serve_start(budget_bytes=64 << 20, max_inflight=16, variant=variant, num_streams=2)
+    try:
+        for r, (ek, ev) in zip(reqs, expected):
+            k, v = to_dev(r.keys), to_dev(r.vals)
+            darm.serve_wait(darm.serve_submit(k, v, descending=r.desc), 120000)
+            assert_equal(f"keys alone (n={r.n})", k.cpu().numpy(), ek)
+            assert_equal(f"payload alone (n={r.n})", v.cpu().numpy(), ev)
+        bufs = [(to_dev(r.keys), to_dev(r.vals)) for r in reqs]
+        ids = [darm.serve_submit(k, v, descending=r.desc) for (k, v), r in zip(bufs, reqs)]
+        for rid in ids:
+            darm.serve_wait(rid, 120000)
+        torch.cuda.synchronize()
+        for r, (ek, ev), (k, v) in zip(reqs, expected, bufs):
+            assert_equal(f"keys mixed (n={r.n})", k.cpu().numpy(), ek)
+            assert_equal(f"payload mixed (n={r.n})", v.cpu().numpy(), ev)
+        assert darm.device_status() == darm.OK
+    finally:
+        darm.serve_stop()
+
+
 def _expected_narrow(words, vals, desc):
     """Service semantics for 32-bit keys: keys are ordered as 32-bit words
     (floats by their totalOrder word) and padding is strictly beyond every

@@ -1,4 +1,4 @@
-"""Pins of the oracle's synthetic divergent kernels (SB1, SB4 and their -R
+"""Pins of the oracle's synthetic divergent kernels (SB1-SB4 and their -R
 variants, Section VI-A), traced by hand.  No GPU needed."""
 import numpy as np
 import pytest
@@ -46,6 +46,30 @@ def test_hand_traces_if_then_regions():
     # SB3-R, thread 2: as SB3 but path 0's second region is 7v - w:
     # j=1 -> s2=7*514-258=3340
     assert _words_of_thread(oracle.sb_run("SB3-R", d, 1, 1), 2) == [2, 776, 3340, 2824]
+
+
+def test_hand_traces_sb1r_sb2r():
+    # SB1-R, thread 1 of data = 0, 1, 2, ... (s = 1, 257, 513, 769); path 0
+    # computes 3v + w, path 1 computes 5v ^ w.  j=0 path 0 (a=0, b=1):
+    # s0=3*1+257=260; j=1 path 1 (a=3, b=0): s3=(5*769)^260=0xF05^0x104=3585;
+    # j=2 path 0 (a=2, b=3): s2=3*513+3585=5124; j=3 path 1 (a=1, b=2):
+    # s1=(5*257)^5124=0x505^0x1404=4353
+    d = np.arange(1024, dtype=np.uint32)
+    assert _words_of_thread(oracle.sb_run("SB1-R", d, 1, 1), 1) == [260, 4353, 5124, 3585]
+    # thread 0 holding s = 1, 3, 5, 7 (every other word 0)
+    d = np.zeros(1024, dtype=np.uint32)
+    d[[0, 256, 512, 768]] = [1, 3, 5, 7]
+    # SB1-R: j=0 path 1 (a=2, b=3): s2=(5*5)^7=25^7=30; j=1 path 0 (a=1, b=2):
+    # s1=3*3+30=39; j=2 path 1 (a=0, b=1): s0=5^39=34; j=3 path 0 (a=3, b=0):
+    # s3=3*7+34=55
+    assert _words_of_thread(oracle.sb_run("SB1-R", d, 1, 1), 0) == [34, 39, 30, 55]
+    # SB2-R: the same paths, each run only if s[b] is odd.  j=0 path 1, s3=7
+    # odd: s2=30; j=1 path 0, s2=30 even: skip; j=2 path 1, s1=3 odd:
+    # s0=5^3=6; j=3 path 0, s0=6 even: skip
+    assert _words_of_thread(oracle.sb_run("SB2-R", d, 1, 1), 0) == [6, 3, 30, 7]
+    # SB2 on the same data: path 1 computes 3v + w as well, so j=0 gives
+    # s2=3*5+7=22 and the rest as above
+    assert _words_of_thread(oracle.sb_run("SB2", d, 1, 1), 0) == [6, 3, 22, 7]
 
 
 def test_blocks_are_independent():
