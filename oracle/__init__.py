@@ -68,6 +68,10 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
             lib.oracle_oddeven_u32.restype = i32
             lib.oracle_oddeven_rec_u32.argtypes = [vp, vp, u64]
             lib.oracle_oddeven_rec_u32.restype = i32
+            for name in ("oracle_pcm_u32", "oracle_pcm_rec_u32"):
+                fn = getattr(lib, name)
+                fn.argtypes = [vp, vp, u64, u64]
+                fn.restype = i32
             lib.oracle_sb.argtypes = [i32, vp, u64, i32, i32]
             lib.oracle_sb.restype = i32
             lib.oracle_compare_exchanges.argtypes = [u64]
@@ -174,6 +178,28 @@ def oddeven_sort(keys, vals=None, recursive=False, mutant=0):
     if rc != OK:
         raise RuntimeError(f"oracle status {rc}")
     return k, v, ncmp
+
+
+def pcm_sort(keys, vals=None, bucket: int = 4096, recursive=False, mutant=0):
+    """PCM (see oracle_pcm_u32 in darm_oracle.c) on copies of uint32 ``keys``
+    (and ``vals``): buckets of ``bucket`` keys sorted by the odd-even merge
+    sort network, then the network over buckets with merge-splits.
+    Returns (keys_out, vals_out or None)."""
+    k = np.ascontiguousarray(keys, dtype=np.uint32).copy()
+    if k.ndim != 1:
+        raise ValueError("keys must be 1-D")
+    v = None
+    if vals is not None:
+        v = np.ascontiguousarray(vals, dtype=np.uint32).copy()
+        if v.shape != k.shape:
+            raise ValueError("vals must match keys")
+    fn = _lib(mutant).oracle_pcm_rec_u32 if recursive else _lib(mutant).oracle_pcm_u32
+    rc = fn(_ptr(k), _ptr(v), k.size, int(bucket))
+    if rc == ERR_NOT_POW2:
+        raise ValueError("bucket size and bucket count must be powers of two")
+    if rc != OK:
+        raise RuntimeError(f"oracle status {rc}")
+    return k, v
 
 
 SB_PATTERNS = {"SB1": 1, "SB2": 2, "SB3": 3, "SB4": 4,

@@ -24,6 +24,9 @@
  *     extreme key before the network runs.
  *   - oracle_oddeven_u32 / oracle_oddeven_rec_u32: Batcher's odd-even merge
  *     sort network (PCM's base, Section VI-A), iterative and recursive.
+ *   - oracle_pcm_u32 / oracle_pcm_rec_u32: PCM (Section VI-A), Batcher's
+ *     network over buckets of sorted keys with merge-split comparators,
+ *     iterative and recursive.
  *   - oracle_sb: the synthetic divergent kernels SB1-SB4 and their -R
  *     variants.
  *
@@ -35,10 +38,12 @@
  *     relative to each other inside one comparator;
  *   - a payload travels with its key; only keys are compared.
  *
- * Status codes: 0 ok, 2 length not a power of two.
+ * Status codes: 0 ok, 1 out of host memory (PCM), 2 length not a power of
+ * two.
  */
 #include <stddef.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #define ORACLE_OK 0
@@ -306,6 +311,125 @@ int oracle_oddeven_rec_u32(uint32_t* key, uint32_t* val, uint64_t n) {
   if (n <= 1) return ORACLE_OK;
   if (!is_pow2_u64(n)) return ORACLE_ERR_NOT_POW2;
   oe_sort(key, val, 0, n);
+  return ORACLE_OK;
+}
+
+/*
+ * PCM, Partition and Concurrent Merge (Section VI-A): a parallel sort built on
+ * Batcher's odd-even merge sort that odd-even merges buckets of sorted
+ * elements.  Reading taken here: the n = B * S keys form B buckets of S
+ * consecutive keys (B and S powers of two); every bucket is sorted by the
+ * odd-even merge sort network above; then the same network runs over the B
+ * buckets, each comparator (bucket x, bucket y), x < y, being a merge-split:
+ * the two sorted buckets are merged - on equal keys bucket x's element comes
+ * first, and within a bucket the order is kept - and the lower S keys of the
+ * merge become bucket x, the upper S bucket y.  With S = 1 a merge-split is a
+ * strict compare-exchange, so PCM is then the plain odd-even network.
+ * Status 2 when B or S is not a power of two (or S does not divide n).
+ */
+/* DARM_ORACLE_MUTANT 8 takes bucket y's element first on equal keys. */
+static void pcm_merge_split(uint32_t* key, uint32_t* val, uint64_t x, uint64_t y, uint64_t S,
+                            uint32_t* tk, uint32_t* tv) {
+  const uint32_t* a = key + x * S;
+  const uint32_t* b = key + y * S;
+  uint64_t i = 0, j = 0;
+  for (uint64_t o = 0; o < 2 * S; ++o) {
+    int take_a;
+    if (i == S)
+      take_a = 0;
+    else if (j == S)
+      take_a = 1;
+    else
+      take_a = (DARM_ORACLE_MUTANT == 8) ? (a[i] < b[j]) : (a[i] <= b[j]);
+    if (take_a) {
+      tk[o] = a[i];
+      if (val) tv[o] = val[x * S + i];
+      ++i;
+    } else {
+      tk[o] = b[j];
+      if (val) tv[o] = val[y * S + j];
+      ++j;
+    }
+  }
+  memcpy(key + x * S, tk, S * sizeof(uint32_t));
+  memcpy(key + y * S, tk + S, S * sizeof(uint32_t));
+  if (val) {
+    memcpy(val + x * S, tv, S * sizeof(uint32_t));
+    memcpy(val + y * S, tv + S, S * sizeof(uint32_t));
+  }
+}
+
+static int pcm_buckets(uint32_t* key, uint32_t* val, uint64_t n, uint64_t S, uint64_t* B) {
+  if (S == 0 || !is_pow2_u64(S) || n % S != 0) return ORACLE_ERR_NOT_POW2;
+  *B = n / S;
+  if (*B == 0) return ORACLE_OK;
+  if (!is_pow2_u64(*B)) return ORACLE_ERR_NOT_POW2;
+  for (uint64_t b = 0; b < *B; ++b)
+    oracle_oddeven_u32(key + b * S, val ? val + b * S : NULL, S, NULL);
+  return ORACLE_OK;
+}
+
+int oracle_pcm_u32(uint32_t* key, uint32_t* val, uint64_t n, uint64_t S) {
+  uint64_t B = 0;
+  const int rc = pcm_buckets(key, val, n, S, &B);
+  if (rc != ORACLE_OK || B < 2) return rc;
+  uint32_t* tk = (uint32_t*)malloc(2 * S * sizeof(uint32_t));
+  uint32_t* tv = (uint32_t*)malloc(2 * S * sizeof(uint32_t));
+  if (!tk || !tv) {
+    free(tk);
+    free(tv);
+    return 1;
+  }
+  /* the iterative network of oracle_oddeven_u32, over bucket indices */
+  for (uint64_t p = 1; p < B; p <<= 1)
+    for (uint64_t k = p; k >= 1; k >>= 1)
+      for (uint64_t j = k % p; j + k < B; j += 2 * k)
+        for (uint64_t i = 0; i < k && i + j + k < B; ++i) {
+          const uint64_t x = i + j;
+          if (x / (2 * p) == (x + k) / (2 * p)) pcm_merge_split(key, val, x, x + k, S, tk, tv);
+        }
+  free(tk);
+  free(tv);
+  return ORACLE_OK;
+}
+
+/* The recursive form over buckets (the recursion of oracle_oddeven_rec_u32
+ * with merge-splits for compare-exchanges). */
+static void pcm_rec_merge(uint32_t* key, uint32_t* val, uint64_t S, uint64_t lo, uint64_t nb,
+                          uint64_t r, uint32_t* tk, uint32_t* tv) {
+  const uint64_t step = 2 * r;
+  if (step < nb) {
+    pcm_rec_merge(key, val, S, lo, nb, step, tk, tv);
+    pcm_rec_merge(key, val, S, lo + r, nb, step, tk, tv);
+    for (uint64_t i = lo + r; i + r < lo + nb; i += step) pcm_merge_split(key, val, i, i + r, S, tk, tv);
+  } else {
+    pcm_merge_split(key, val, lo, lo + r, S, tk, tv);
+  }
+}
+
+static void pcm_rec_sort(uint32_t* key, uint32_t* val, uint64_t S, uint64_t lo, uint64_t nb,
+                         uint32_t* tk, uint32_t* tv) {
+  if (nb < 2) return;
+  const uint64_t h = nb / 2;
+  pcm_rec_sort(key, val, S, lo, h, tk, tv);
+  pcm_rec_sort(key, val, S, lo + h, h, tk, tv);
+  pcm_rec_merge(key, val, S, lo, nb, 1, tk, tv);
+}
+
+int oracle_pcm_rec_u32(uint32_t* key, uint32_t* val, uint64_t n, uint64_t S) {
+  uint64_t B = 0;
+  const int rc = pcm_buckets(key, val, n, S, &B);
+  if (rc != ORACLE_OK || B < 2) return rc;
+  uint32_t* tk = (uint32_t*)malloc(2 * S * sizeof(uint32_t));
+  uint32_t* tv = (uint32_t*)malloc(2 * S * sizeof(uint32_t));
+  if (!tk || !tv) {
+    free(tk);
+    free(tv);
+    return 1;
+  }
+  pcm_rec_sort(key, val, S, 0, B, tk, tv);
+  free(tk);
+  free(tv);
   return ORACLE_OK;
 }
 
