@@ -1,4 +1,4 @@
-"""Oracle for the melding analysis (Section IV-E): TEST INFRASTRUCTURE ONLY
+"""Oracle for the melding analysis (Section IV-C): TEST INFRASTRUCTURE ONLY
 (the tests use it; the library never does).  Plain Python restatements of
 the paper's definitions, written independently of the C ABI tool:
 
@@ -14,6 +14,20 @@ the paper's definitions, written independently of the C ABI tool:
 
 An instruction is (opcode, type, latency); two instructions are compatible
 (can be aligned) when opcode and type are equal.
+
+Subgraphs (Def. 3, Def. 6, Def. 7) are (blocks, shape, simple_region):
+blocks in pre-order, `shape` naming the structure (two multi-block subgraphs
+are isomorphic when their shapes and block counts agree):
+
+* sese_profit(s1, s2): Def. 6's three cases - isomorphic multi-block
+  subgraphs: MP_S of corresponding blocks; two single blocks: MP_B; a single
+  block A and a simple region M: the region replicated around A, A beside
+  its most profitable partner E and every other replicated block empty, so
+  MP_S = MP_B(A, E) (lat(A) + lat(E)) / (lat(A) + lat(M)); anything else is
+  not meldable (None);
+* best_subgraph_alignment_score(t, f, gap): the optimal subgraph alignment
+  by brute force over every chain of meldable pairs, scored like the
+  instruction alignment with MP as the pair score.
 """
 from __future__ import annotations
 
@@ -61,6 +75,51 @@ def best_local_alignment_score(a, b, gap: float) -> float:
             i, j = pairs[k]
             if not chain or (i > chain[-1][0] and j > chain[-1][1]):
                 extend(chain + [(i, j)], k + 1)
+
+    extend([], 0)
+    return best
+
+
+def sese_profit(s1, s2):
+    b1, shape1, simple1 = s1
+    b2, shape2, simple2 = s2
+    if len(b1) == 1 and len(b2) == 1:
+        return mp_block(b1[0], b2[0])
+    if len(b1) > 1 and len(b2) > 1:
+        if len(b1) != len(b2) or shape1 != shape2:
+            return None
+        return mp_subgraph(b1, b2)
+    # a single block beside a region: replicate the region around it
+    (single, _, _), (region, _, simple) = (s1, s2) if len(b1) == 1 else (s2, s1)
+    if not simple:
+        return None
+    a = single[0]
+    # the region's block with the highest MP_B; the first one on ties
+    k_best = max(range(len(region)), key=lambda k: (mp_block(a, region[k]), -k))
+    replica = [[] for _ in region]
+    replica[k_best] = a
+    return mp_subgraph(replica, region)
+
+
+def best_subgraph_alignment_score(t, f, gap: float) -> float:
+    cand = []
+    for i in range(len(t)):
+        for j in range(len(f)):
+            mp = sese_profit(t[i], f[j])
+            if mp is not None:
+                cand.append((i, j, mp))
+    best = 0.0
+
+    def extend(chain, start):
+        nonlocal best
+        if chain:
+            (i0, j0, _), (i1, j1, _) = chain[0], chain[-1]
+            unaligned = (i1 - i0 + 1 - len(chain)) + (j1 - j0 + 1 - len(chain))
+            best = max(best, sum(c[2] for c in chain) - gap * unaligned)
+        for k in range(start, len(cand)):
+            i, j, _ = cand[k]
+            if not chain or (i > chain[-1][0] and j > chain[-1][1]):
+                extend(chain + [cand[k]], k + 1)
 
     extend([], 0)
     return best
