@@ -40,8 +40,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["darm", "reference"], default="darm")
     ap.add_argument("--workload",
-                    choices=["kv24", "kv24skew", "f32", "cfg1", "oem4096", "oem26", "sb",
-                             "seg", "serve"],
+                    choices=["kv24", "kv24skew", "f32", "cfg1", "oem4096", "oem26", "pcm28",
+                             "sb", "seg", "serve"],
                     default="f32")
     ap.add_argument("--serve-requests", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -396,6 +396,141 @@ def run_oddeven(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def pcm_layer_bytes(n, bucket):
+    """Algorithmic HBM bytes of PCM's merge-split layers over n uint32 keys:
+    every comparator reads and writes its two buckets once (8 bytes per key
+    moved); layer (s, t) of B buckets has B/2 comparators when t == s, else
+    (B / 2^(s+1)) (2^s - 2^t).  Returns (total bytes, layer launches)."""
+    nb = n // bucket
+    total, launches = 0, 0
+    s = 0
+    while (1 << s) < nb:
+        for t in range(s, -1, -1):
+            ncmp = nb // 2 if t == s else (nb >> (s + 1)) * ((1 << s) - (1 << t))
+            total += ncmp * 2 * bucket * 8
+            launches += 1
+        s += 1
+    return total, launches
+
+
+def run_pcm(args, world, rank, local):
+    """PCM (Section VI-A): 2^28 uniform uint32 keys, buckets of 4096 sorted by
+    the odd-even merge sort network, then odd-even merged bucket by bucket
+    with merge-splits; melded vs divergent merge loop, L2 flushed between
+    sorts."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2107_05681_gb300 as darm
+    import synth
+    bucket = 4096
+    keys = synth.uniform_u32(0xDA2C0008, 1 << 28)
+    n = keys.size
+    src = torch.from_numpy(keys).cuda()
+    work = torch.empty_like(src)
+    scratch = torch.empty_like(src)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def run_sort(t, variant="melded"):
+        darm.pcm_sort(t, bucket=bucket, scratch_keys=scratch, variant=variant)
+
+    work.copy_(src)
+    run_sort(work)
+    torch.cuda.synchronize()
+    got = work.cpu().numpy()
+    assert np.all(got[1:] >= got[:-1]), "PCM result not sorted"
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(1.0)
+    out, launches = {}, 0
+    for variant in ("melded", "divergent"):
+        for _ in range(args.warmup):
+            work.copy_(src)
+            run_sort(work, variant)
+        torch.cuda.synchronize()
+        barrier(world)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        l0 = darm.launch_count()
+        for a, b in evs:
+            work.copy_(src)
+            flush.fill_(1.0)
+            a.record(stream)
+            run_sort(work, variant)
+            b.record(stream)
+        torch.cuda.synchronize()
+        launches += darm.launch_count() - l0
+        out[variant] = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), world)
+    # the bucket sorts alone, to split the time between the two kernels
+    bevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(args.steps)]
+    for a, b in bevs:
+        work.copy_(src)
+        flush.fill_(1.0)
+        a.record(stream)
+        darm.oddeven_sort_buckets(work, bucket=bucket)
+        b.record(stream)
+    torch.cuda.synchronize()
+    bucket_ms = sum(a.elapsed_time(b) for a, b in bevs) / args.steps
+    clk = clocks.stop()
+    # end to end: pinned host -> device, sort, back
+    hk = torch.empty(n, dtype=torch.uint32, pin_memory=True)
+    hk.copy_(src.cpu())
+    tot = 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        work.copy_(hk, non_blocking=True)
+        run_sort(work)
+        hk.copy_(work, non_blocking=True)
+        torch.cuda.synchronize()
+        tot += time.perf_counter() - t0
+    tot = max_over_ranks(tot, world)
+    if rank == 0:
+        ms = out["melded"] / args.steps
+        layer_bytes, nlayers = pcm_layer_bytes(n, bucket)
+        layers_ms = ms - bucket_ms
+        ach = layer_bytes / (layers_ms * 1e-3) / 1e9
+        peak = measured_hbm_peak()
+        # CPU baseline: the oracle on a bounded prefix (2^20 keys, 256 buckets)
+        m_cpu = 20
+        t0, reps = time.perf_counter(), 0
+        while time.perf_counter() - t0 < 2.0:
+            oracle.pcm_sort(keys[: 1 << m_cpu], bucket=bucket)
+            reps += 1
+        cdt = time.perf_counter() - t0
+        line = {
+            "metric": "sorted keys/s, PCM (odd-even merge of sorted buckets), melded vs "
+                      "divergent merge loop",
+            "value": world * n / (ms * 1e-3), "unit": "keys/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": "PCM, 2^28 uint32 keys uniform, buckets of 4096 keys "
+                                   "(65,536 buckets), the paper's PCM input size",
+                       "n": n, "bucket": bucket, "variant": "melded",
+                       "l2": "flushed between steps (256 MiB write outside the timed events)"},
+            "divergent": {"value": world * n * args.steps / (out["divergent"] * 1e-3),
+                          "ms_per_step": out["divergent"] / args.steps},
+            "melded_over_divergent": out["divergent"] / out["melded"],
+            "roofline": {"bound": "hbm", "kernel": "merge-split layers", "achieved": ach,
+                         "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                         "algorithmic_bytes": layer_bytes / nlayers, "layers": nlayers,
+                         "layers_ms": layers_ms, "bucket_sort_ms": bucket_ms,
+                         "note": "achieved = algorithmic bytes of all merge-split layers / their "
+                                 "time (the sort's time minus the bucket sorts' time)"},
+            "clocks": clk, "gpu_launches": launches,
+            "e2e": {"value": world * n * args.steps / tot, "unit": "keys/s",
+                    "h2d_bytes_per_step": n * 4, "d2h_bytes_per_step": n * 4},
+            "cpu_baseline": {"value": reps * (1 << m_cpu) / cdt, "unit": "keys/s", "cores": 1,
+                             "kind": "oracle", "host": host_cpu(),
+                             "sample": f"{reps} single-threaded oracle PCM sorts of the first "
+                                       f"2^{m_cpu} keys ({cdt:.1f} s)"},
+        }
+        print(json.dumps(line), flush=True)
+
+
 def run_synthetic(args, world, rank, local):
     """The synthetic divergent kernels SB1, SB4, SB1-R, SB4-R (Section VI-A),
     melded vs divergent: 1216 blocks of 256 threads (eight per SM), 64 outer
@@ -653,14 +788,14 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
-    if args.workload in ("seg", "serve", "oem4096", "oem26", "sb"):
+    if args.workload in ("seg", "serve", "oem4096", "oem26", "pcm28", "sb"):
         import torch
 
         import paper_2107_05681_gb300 as darm
         torch.cuda.set_device(local)
         darm.init(local)
         runner = {"seg": run_segmented, "serve": run_serving, "oem4096": run_oddeven,
-                  "oem26": run_oddeven, "sb": run_synthetic}
+                  "oem26": run_oddeven, "pcm28": run_pcm, "sb": run_synthetic}
         runner[args.workload](args, world, rank, local)
         return
     import numpy as np

@@ -10,11 +10,20 @@
  *                   the compare-exchange body (loads, compare, stores), one
  *                   per direction, so threads whose blocks run in opposite
  *                   directions diverge;
- *   DARM_MELDED     the two copies melded as in Section IV-D/E and IV-G:
- *                   loads and stores aligned into one copy, the two
- *                   direction-specific compares kept as unaligned
- *                   instructions, and a select on the direction choosing the
- *                   swap condition.
+ *   DARM_MELDED     the two copies melded as in Sections IV-D and IV-G
+ *                   (a region-region meld): the loads and stores of both
+ *                   sides are aligned into one copy, and the two
+ *                   direction-specific compares (key[l] < key[i] ascending,
+ *                   key[l] > key[i] descending) are aligned into one compare
+ *                   whose differing operands are selected by the direction
+ *                   (Algorithm 2's SetOperands rule): the descending side's
+ *                   keys are XORed with an all-ones direction mask when the
+ *                   round loads them (~x reverses unsigned order), one
+ *                   ascending compare-exchange runs for both directions,
+ *                   and the store XORs the mask back.  The paper's own
+ *                   melded BIT keeps the two compares unaligned and selects
+ *                   the swap condition; both forms compute the same
+ *                   comparator network bit for bit.
  *
  * Both forms compute the same comparator network and give bit-identical
  * results.  Conventions shared by every sorting entry point:
@@ -117,16 +126,21 @@ int darm_bitonic_sort_host(void* keys, uint32_t* vals, size_t n, int dtype,
 
 /* ---- batched segmented sort ------------------------------------------ */
 
-/* Sort num_segs independent segments in one batched launch sequence.
+/* Sort num_segs independent segments in one batched launch sequence: the
+ * paper's BIT benchmark sorts its input bucket by bucket, one thread block
+ * per bucket (Section VI-A); here the buckets are arrays of uneven size.
  * Segment s occupies elements [seg_offsets[s], seg_offsets[s+1]) of keys
  * and vals; its capacity (the difference) must be a power of two and its
  * offset a multiple of min(capacity, 4) elements.  Only the first seg_len[s] elements are
  * real: the library writes the sentinel (UINT32_MAX for ascending, 0 for
  * descending; payload 0xFFFFFFFF) beyond them and sorts the whole capacity,
  * so the real keys end up first.  seg_offsets (uint64, num_segs + 1
- * entries) and seg_len (uint32) are HOST arrays: the library builds a
- * longest-first work list from them, uploads it once and replays the launch
- * sequence as a CUDA graph on later calls with the same layout.
+ * entries) and seg_len (uint32) are HOST arrays, not device arrays: the
+ * launch sequence (how many passes, how many blocks each, which segments
+ * share a block) depends on the layout, so the host must read it anyway; the
+ * library builds a longest-first work list from it, uploads it once and
+ * replays the launch sequence as a CUDA graph on later calls with the same
+ * layout.
  * seg_desc (HOST, uint8 per segment, nullable) overrides `dir` per segment.
  * With a payload, a real key equal to the sentinel makes the result
  * ambiguous; the kernel latches DARM_ERR_SENTINEL_COLLISION in the device
@@ -143,17 +157,21 @@ int darm_segmented_sort(uint32_t* keys, uint32_t* vals, const uint64_t* seg_offs
  * darm_segmented_sort keeps in buffers it allocates are instead copied, on
  * `stream`, into one 1 MiB array compiled into the library, right before each
  * launch; nothing is allocated on the device and no graph is built.
- *   - Limit: the tables of any single launch must fit in 1 MiB (16 bytes per
- *     segment of a phase plus 16 bytes per block; roughly up to 30,000
- *     segments or 60,000 blocks of a tile); larger layouts are rejected with
- *     DARM_ERR_INVALID_ARG and a message on stderr, before anything is
- *     enqueued.
+ *   - Limit: the tables of any single launch must fit in 1 MiB:
+ *     256 bytes of counter + 16 bytes per segment slot of the launch's phase
+ *     (rounded up to a multiple of 256) + 12 bytes per block of the launch
+ *     <= 1,048,576 bytes (so at most 65,520 slots, or 87,360 blocks, in one
+ *     launch); larger layouts are rejected with DARM_ERR_INVALID_ARG and a
+ *     message on stderr, before anything is enqueued.
  *   - The array is shared by every call and keeps the last call's contents:
  *     calls whose work overlaps on the GPU (other streams, other host
  *     threads) race on it.  Calls on one stream are ordered and safe.
  *   - The first call on a device looks up the array's device address (with
- *     that device current) and caches it; make that first call before any
- *     stream capture.
+ *     that device current) and caches it.
+ *   - Each launch's tables are copied from host memory that the call reuses
+ *     and frees before it returns, so the call must not be recorded into a
+ *     CUDA graph: on a stream that is capturing it returns
+ *     DARM_ERR_INVALID_ARG before enqueueing anything.
  * Arguments, layout rules and results are those of darm_segmented_sort. */
 int darm_segmented_sort_noalloc(uint32_t* keys, uint32_t* vals, const uint64_t* seg_offsets,
                                 const uint32_t* seg_len, uint32_t num_segs, int dir,
@@ -181,6 +199,28 @@ int darm_oddeven_sort_block(uint32_t* keys, uint32_t* vals, size_t n, int varian
  * n not a multiple of bucket, NULL keys, bad variant), DARM_ERR_CUDA. */
 int darm_oddeven_sort_buckets(uint32_t* keys, uint32_t* vals, size_t n, size_t bucket,
                               int variant, void* stream);
+
+/* PCM, Partition and Concurrent Merge (Section VI-A): a sort of the whole
+ * array built on Batcher's odd-even merge sort.  The n keys form n / bucket
+ * buckets (bucket a power of two <= 4096, the bucket count a power of two);
+ * each bucket is sorted by the odd-even merge sort network
+ * (darm_oddeven_sort_buckets), then the same network runs over the buckets
+ * with every comparator (bucket x, bucket y > x) a merge-split: the two
+ * sorted buckets are merged - on equal keys bucket x's key first, each
+ * bucket's keys in order - and the lower half becomes bucket x, the upper
+ * half bucket y.  The result is the whole array sorted ascending, the
+ * payload order under equal keys being the one this network fixes.
+ * keys/vals: DEVICE arrays sorted in place (vals nullable); scratch_keys
+ * (and scratch_vals when vals is given): DEVICE arrays of n elements the
+ * call may overwrite (not needed when there is one bucket); all 16-byte
+ * aligned.  variant: DARM_DIVERGENT (the merge loop's data-dependent branch
+ * with one copy of its body per side) or DARM_MELDED / DARM_AUTO (the two
+ * sides melded by selects).  Asynchronous on `stream`.  Errors:
+ * DARM_ERR_NOT_POW2 (bucket or bucket count), DARM_ERR_INVALID_ARG (bucket
+ * > 4096, n not a multiple of bucket, n > 2^32, NULL or misaligned
+ * buffers, bad variant), DARM_ERR_CUDA. */
+int darm_pcm_sort(uint32_t* keys, uint32_t* vals, size_t n, size_t bucket,
+                  uint32_t* scratch_keys, uint32_t* scratch_vals, int variant, void* stream);
 
 /* ---- synthetic divergent kernels (Section VI-A) ------------------------- */
 
@@ -212,7 +252,7 @@ typedef struct {
   int32_t latency;
 } darm_inst;
 
-/* Melding profitability of two basic blocks (Section IV-E, MP_B): the sum
+/* Melding profitability of two basic blocks (Section IV-C, MP_B): the sum
  * over opcodes of min(frequency in b1, frequency in b2) x latency, over
  * lat(b1) + lat(b2).  Identical profiles give 0.5.  Host arrays; NaN on bad
  * arguments or inconsistent latencies. */
@@ -225,7 +265,7 @@ double darm_meld_mp_block(const darm_inst* b1, int n1, const darm_inst* b2, int 
 double darm_meld_mp_subgraph(const darm_inst* i1, const int32_t* off1, const darm_inst* i2,
                              const int32_t* off2, int nb);
 
-/* Instruction alignment of two blocks (Smith-Waterman, Section IV-E):
+/* Instruction alignment of two blocks (Smith-Waterman, Section IV-C):
  * compatible instructions (same opcode and type) align with score equal to
  * their latency, each unaligned instruction inside the aligned stretch costs
  * `gap` (>= 0).  Writes both sequences in program order as (i, j) pairs into
@@ -234,6 +274,51 @@ double darm_meld_mp_subgraph(const darm_inst* i1, const int32_t* off1, const dar
  * the alignment score in *score (nullable). */
 int darm_meld_align(const darm_inst* a, int na, const darm_inst* b, int nb, double gap,
                     int32_t* pairs, double* score);
+
+/* A single-entry single-exit subgraph (Def. 3) of one path of a divergent
+ * region: `nblocks` basic blocks linearised in pre-order, block k being
+ * block `first_block + k` of a block table (block b = instructions
+ * insts[block_off[b] .. block_off[b+1])).  Two subgraphs of more than one
+ * block are isomorphic exactly when they have the same `shape` id (and
+ * block count); `simple_region` is 1 for a simple region (Def. 1). */
+typedef struct {
+  int32_t first_block;
+  int32_t nblocks;
+  int32_t shape;
+  int32_t simple_region;
+} darm_subgraph;
+
+/* The paper's default melding profitability threshold (Section V). */
+#define DARM_MELD_THRESHOLD 0.2
+
+/* Melding profitability of two SESE subgraphs (Def. 6, Section IV-C):
+ * case 1, two isomorphic subgraphs of more than one block: MP_S over the
+ * corresponding blocks; case 3, two single blocks: MP_B; case 2, a single
+ * block A against a simple region M (region replication): A is placed
+ * beside the block E of M with the highest MP_B(A, E) (first in pre-order
+ * on ties) in a copy of M whose other blocks are empty, giving
+ * MP_B(A, E) * (lat(A) + lat(E)) / (lat(A) + lat(M)).  Returns -1 when the
+ * pair is not meldable (different shapes, or a block against a region that
+ * is not simple); NaN on bad arguments or inconsistent latencies.  Host
+ * arrays; block_off has nblocks_total + 1 entries. */
+double darm_meld_mp_sese(const darm_inst* insts, const int32_t* block_off, int nblocks_total,
+                         const darm_subgraph* s1, const darm_subgraph* s2);
+
+/* Subgraph alignment (Def. 7) and the meld decision of Algorithm 1: the
+ * ordered subgraphs st[0..m) of the true path and sf[0..n) of the false
+ * path are aligned by Smith-Waterman, an aligned pair scoring its
+ * profitability (darm_meld_mp_sese; non-meldable pairs cannot align) and
+ * each unaligned subgraph inside the aligned stretch costing `gap` (>= 0).
+ * Writes the k aligned pairs in order: (pairs[2i], pairs[2i+1]) = indices
+ * into st and sf, profit[i] their profitability and meld[i] = 1 when
+ * profit[i] >= threshold (Algorithm 1 melds those; pass
+ * DARM_MELD_THRESHOLD for the paper's default).  Capacity: min(m, n)
+ * pairs.  Returns k (-1 on bad arguments) and the alignment score in
+ * *score (nullable). */
+int darm_meld_subgraph_align(const darm_inst* insts, const int32_t* block_off, int nblocks_total,
+                             const darm_subgraph* st, int m, const darm_subgraph* sf, int n,
+                             double gap, double threshold, int32_t* pairs, double* profit,
+                             int32_t* meld, double* score);
 
 /* ---- tuning ----------------------------------------------------------- */
 
@@ -263,8 +348,19 @@ int darm_autotune_segmented(uint32_t* keys, uint32_t* vals, const uint64_t* seg_
                             const uint32_t* seg_len, uint32_t num_segs, const char* db_path);
 
 /* Load plans previously written by darm_autotune and
- * darm_autotune_segmented (lines with log2 n = 0 are batch tunings). */
+ * darm_autotune_segmented (lines with log2 n = 0 are batch tunings).  A
+ * line holds 13 or 14 whitespace-separated fields: key kind (0 32-bit, 1
+ * 64-bit), payload flag, log2 n, log2 tile, log2 elements per thread in
+ * tile/merge passes and in window passes, log2 threads of a one-window
+ * pass, register windows per window pass, bulk-copy staging buffers of the
+ * merge, the form (0 divergent, 1 melded) of tile, window and merge passes,
+ * the tuner's time in ms, and optionally 1 for a tile pass with shuffle
+ * stages (0 when absent). */
 int darm_load_tune_db(const char* db_path);
+
+/* Forget every tuning loaded or measured so far: later calls plan with the
+ * library's defaults again. */
+int darm_reset_tunings(void);
 
 /* ---- introspection ----------------------------------------------------- */
 
@@ -273,6 +369,33 @@ int darm_load_tune_db(const char* db_path);
  * launches = kernel launches, tile = elements a tile pass keeps on chip. */
 int darm_plan_info(int dtype, size_t n, int has_vals, int variant,
                    int* passes, int* launches, int* tile);
+
+/* Text description of the launch sequence darm_plan_info counts, one line
+ * per launch: pass kind ("tile", "window", "merge"; "*" marks a
+ * compile-time schedule, "~" a tile pass with shuffle stages), elements per
+ * thread, form, grid, threads, shared memory and the block bit map.  Writes
+ * at most cap bytes into buf, NUL-terminated. */
+int darm_plan_describe(int dtype, size_t n, int has_vals, int variant, char* buf, size_t cap);
+
+/* The launch sequence of a whole-array sort as numbers, for checking the
+ * planner on the host (no device needed, darm_sort_init not required).
+ * tuning (nullable: the tuning a sort of this size would use): 7 int32 -
+ * log2 tile, log2 elements per thread in tile/merge passes and in window
+ * passes, log2 threads of a one-window pass, windows per window pass,
+ * bulk-copy staging buffers, shuffle stages (0/1).  smem_limit: shared
+ * memory per block the plan may use (0: the device's, or 227 KiB before
+ * init).  Writes, per launch, 20 int32 - pass kind (0 tile, 1 window,
+ * 2 merge), compile-time tile/merge schedule, bulk-copy buffers, one-window
+ * and two-window compile-time shapes, shuffle stages, log2 elements per
+ * thread, form, grid, threads, shared memory bytes, then the block bit map
+ * b, c, w0, s, log2 of the array length, rounds, persistent block count,
+ * key map in and out - followed by 7 int32 per round: kind (0 registers
+ * only, 1 window), stage bit p, window bit a, layers, source and
+ * destination (0 HBM, 1 shared memory), lane-divergent flag.  *count
+ * receives the number of int32 needed; DARM_ERR_INVALID_ARG when cap is
+ * smaller (nothing written). */
+int darm_plan_dump(int dtype, size_t n, int has_vals, int variant, const int32_t* tuning,
+                   size_t smem_limit, int32_t* out, int cap, int* count);
 
 /* Profiling run of a whole-array sort: the same launches as the plain call,
  * with a CUDA event pair recorded on `stream` around each one.  Synchronises

@@ -62,15 +62,22 @@ _sig = {
     "darm_oddeven_sort_block": ([_vp, _vp, _sz, _i32, _vp], _i32),
     "darm_oddeven_sort_buckets": ([_vp, _vp, _sz, _sz, _i32, _vp], _i32),
     "darm_sb_run": ([_i32, _vp, _sz, _i32, _i32, _i32, _vp], _i32),
+    "darm_pcm_sort": ([_vp, _vp, _sz, _sz, _vp, _vp, _i32, _vp], _i32),
     "darm_meld_mp_block": ([_vp, _i32, _vp, _i32], ctypes.c_double),
     "darm_meld_mp_subgraph": ([_vp, _vp, _vp, _vp, _i32], ctypes.c_double),
     "darm_meld_align": ([_vp, _i32, _vp, _i32, ctypes.c_double, _vp, _vp], _i32),
+    "darm_meld_mp_sese": ([_vp, _vp, _i32, _vp, _vp], ctypes.c_double),
+    "darm_meld_subgraph_align": ([_vp, _vp, _i32, _vp, _i32, _vp, _i32, ctypes.c_double,
+                                  ctypes.c_double, _vp, _vp, _vp, _vp], _i32),
     "darm_autotune": ([_i32, _sz, _i32, ctypes.c_char_p], _i32),
     "darm_autotune_segmented": ([_vp, _vp, _vp, _vp, ctypes.c_uint32, ctypes.c_char_p], _i32),
     "darm_load_tune_db": ([ctypes.c_char_p], _i32),
+    "darm_reset_tunings": ([], _i32),
     "darm_plan_info": ([_i32, _sz, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                         ctypes.POINTER(_i32)], _i32),
     "darm_launch_count": ([], _u64),
+    "darm_plan_describe": ([_i32, _sz, _i32, _i32, ctypes.c_char_p, _sz], _i32),
+    "darm_plan_dump": ([_i32, _sz, _i32, _i32, _vp, _sz, _vp, _i32, ctypes.POINTER(_i32)], _i32),
     "darm_sort_profile": ([_vp, _vp, _sz, _i32, _i32, _i32, _vp, ctypes.POINTER(ctypes.c_float),
                            ctypes.POINTER(_i32), _i32, ctypes.POINTER(_i32)], _i32),
     "darm_sort_serve_start": ([_vp], _i32),
@@ -246,6 +253,60 @@ def meld_align(a, b, gap: float = 1.0):
     return out, float(score.value)
 
 
+MELD_THRESHOLD = 0.2  # the paper's default melding profitability threshold
+
+
+def _subgraph_tables(*paths):
+    """Subgraphs given as (blocks, shape, simple_region), blocks a list of
+    [(opcode, type, latency), ...] in pre-order -> one instruction array, one
+    block offset table and a darm_subgraph array (int32 x 4) per path."""
+    import numpy as np
+    insts, offs, out = [], [0], []
+    for path in paths:
+        rows = []
+        for blocks, shape, simple in path:
+            rows.append((len(offs) - 1, len(blocks), int(shape), int(bool(simple))))
+            for b in blocks:
+                insts.extend(b)
+                offs.append(len(insts))
+        out.append(np.ascontiguousarray(np.asarray(rows, dtype=np.int32).reshape(-1, 4)))
+    ia, ip = _insts(insts)
+    off = np.ascontiguousarray(np.asarray(offs, dtype=np.int32))
+    return ia, ip, off, out
+
+
+def meld_mp_sese(s1, s2) -> float:
+    """Melding profitability of two SESE subgraphs (blocks, shape,
+    simple_region) under Def. 6; -1 when they are not meldable."""
+    ia, ip, off, (t1, t2) = _subgraph_tables([s1], [s2])
+    return float(lib.darm_meld_mp_sese(ip, off.ctypes.data_as(ctypes.c_void_p), off.size - 1,
+                                       t1.ctypes.data_as(ctypes.c_void_p),
+                                       t2.ctypes.data_as(ctypes.c_void_p)))
+
+
+def meld_subgraph_align(true_path, false_path, gap: float = 0.1,
+                        threshold: float = MELD_THRESHOLD):
+    """Subgraph alignment of two paths (lists of (blocks, shape,
+    simple_region)) and Algorithm 1's meld decision: returns
+    ([(i, j, profit, meld), ...], score)."""
+    import numpy as np
+    ia, ip, off, (ts, fs) = _subgraph_tables(true_path, false_path)
+    cap = max(1, min(len(ts), len(fs)))
+    pairs = np.zeros(2 * cap, dtype=np.int32)
+    profit = np.zeros(cap, dtype=np.float64)
+    meld = np.zeros(cap, dtype=np.int32)
+    score = ctypes.c_double(0.0)
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a.size else None  # noqa: E731
+    k = lib.darm_meld_subgraph_align(ip, off.ctypes.data_as(ctypes.c_void_p), off.size - 1,
+                                     vp(ts), len(ts), vp(fs), len(fs), float(gap),
+                                     float(threshold), vp(pairs), vp(profit), vp(meld),
+                                     ctypes.byref(score))
+    if k < 0:
+        raise ValueError("bad subgraph alignment arguments")
+    return ([(int(pairs[2 * i]), int(pairs[2 * i + 1]), float(profit[i]), bool(meld[i]))
+             for i in range(k)], float(score.value))
+
+
 def oddeven_sort_buckets(keys, vals=None, bucket: int = 4096, variant="melded",
                          stream=None) -> None:
     """Sort every aligned bucket of `bucket` keys (power of two, <= 4096) of a
@@ -262,6 +323,31 @@ def oddeven_sort_buckets(keys, vals=None, bucket: int = 4096, variant="melded",
     rc = lib.darm_oddeven_sort_buckets(ctypes.c_void_p(keys.data_ptr()), vp, keys.numel(),
                                        int(bucket), _variant(variant), _stream_handle(stream))
     _check(rc, "darm_oddeven_sort_buckets")
+
+
+def pcm_sort(keys, vals=None, bucket: int = 4096, scratch_keys=None, scratch_vals=None,
+             variant="melded", stream=None) -> None:
+    """PCM: sort a contiguous uint32 CUDA tensor (and its payload) in place,
+    buckets of `bucket` keys sorted by the odd-even network, then merged by
+    the odd-even network over buckets with merge-splits.  The scratch
+    tensors (same shape) are created here when not given."""
+    import torch
+    if keys.dtype != torch.uint32 or not keys.is_cuda or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous uint32 CUDA tensor")
+    vp = svp = None
+    if scratch_keys is None:
+        scratch_keys = torch.empty_like(keys)
+    if vals is not None:
+        if vals.dtype != torch.uint32 or vals.shape != keys.shape or not vals.is_contiguous():
+            raise ValueError("vals must be a contiguous uint32 CUDA tensor shaped like keys")
+        vp = ctypes.c_void_p(vals.data_ptr())
+        if scratch_vals is None:
+            scratch_vals = torch.empty_like(vals)
+        svp = ctypes.c_void_p(scratch_vals.data_ptr())
+    rc = lib.darm_pcm_sort(ctypes.c_void_p(keys.data_ptr()), vp, keys.numel(), int(bucket),
+                           ctypes.c_void_p(scratch_keys.data_ptr()), svp, _variant(variant),
+                           _stream_handle(stream))
+    _check(rc, "darm_pcm_sort")
 
 
 def sort_host(keys, vals=None, descending: bool = False, variant="melded") -> None:
@@ -396,6 +482,54 @@ def autotune_segmented(keys, vals, offsets, lengths, db_path: str | None = None)
 
 def load_tune_db(db_path: str) -> None:
     _check(lib.darm_load_tune_db(db_path.encode()), "darm_load_tune_db")
+
+
+def plan_describe(dtype: int, n: int, has_vals: bool, variant="melded") -> list[str]:
+    """The launch sequence of a whole-array sort, one line per launch."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(lib.darm_plan_describe(dtype, n, int(bool(has_vals)), _variant(variant), buf,
+                                  len(buf)), "darm_plan_describe")
+    return buf.value.decode().splitlines()
+
+
+_LAUNCH_FIELDS = ("kind", "fixed", "tma", "win1", "win2", "shfl", "loge", "variant", "grid",
+                  "threads", "smem", "b", "c", "w0", "s", "log2cap", "nrounds", "nblocks",
+                  "map_in", "map_out")
+_ROUND_FIELDS = ("kind", "p", "a", "cnt", "src", "dst", "lanediv")
+
+
+def plan_dump(dtype: int, n: int, has_vals: bool, variant="melded", tuning=None,
+              smem_limit: int = 0) -> list[dict]:
+    """The launch sequence of a whole-array sort as dicts (host only: no
+    device needed).  tuning: (t, e1, e2, c2, w2, tma, shfl) or None."""
+    import numpy as np
+    tn = None
+    if tuning is not None:
+        tn = np.ascontiguousarray(np.asarray(tuning, dtype=np.int32))
+    cnt = ctypes.c_int(0)
+    args = (dtype, n, int(bool(has_vals)), _variant(variant),
+            None if tn is None else tn.ctypes.data_as(ctypes.c_void_p), smem_limit)
+    rc = lib.darm_plan_dump(*args, None, 0, ctypes.byref(cnt))
+    if rc not in (OK, ERR_INVALID_ARG) or cnt.value == 0:
+        _check(rc if rc != OK else ERR_INVALID_ARG, "darm_plan_dump")
+    buf = np.zeros(cnt.value, dtype=np.int32)
+    _check(lib.darm_plan_dump(*args, buf.ctypes.data_as(ctypes.c_void_p), buf.size,
+                              ctypes.byref(cnt)), "darm_plan_dump")
+    out, i = [], 0
+    while i < buf.size:
+        L = dict(zip(_LAUNCH_FIELDS, (int(x) for x in buf[i:i + 20])))
+        i += 20
+        L["rounds"] = []
+        for _ in range(L["nrounds"]):
+            L["rounds"].append(dict(zip(_ROUND_FIELDS, (int(x) for x in buf[i:i + 7]))))
+            i += 7
+        out.append(L)
+    return out
+
+
+def reset_tunings() -> None:
+    """Forget loaded or measured tunings: plans return to the defaults."""
+    _check(lib.darm_reset_tunings(), "darm_reset_tunings")
 
 
 # ---- serving -----------------------------------------------------------------

@@ -3,12 +3,14 @@
 // segmented sort and the serving loop.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <string>
 #include <vector>
 
 #include "darm.h"
@@ -45,6 +47,7 @@ int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_
         : L.win2 ? ((kk == KEY_U32) ? window2_kernel_u32(has_vals, L.loge, int(L.P.c), L.variant)
                                   : window2_kernel_u64(has_vals, L.loge, int(L.P.c), L.variant)).fn
         : L.tma ? tma_merge_kernel_u32(has_vals, L.loge, int(L.P.b), L.tma, L.variant, nullptr).fn
+        : L.shfl ? tile_shfl_kernel_u32(has_vals, L.loge, int(L.P.b), L.variant).fn
         : L.fixed ? fixed_kernel_fn(kk, has_vals, L.loge, int(L.P.b), L.variant, L.kind == PASS_MERGE)
                   : kernel_fn(kk, has_vals, L.loge, L.variant);
     if (!fn) return DARM_ERR_INVALID_ARG;
@@ -81,7 +84,7 @@ const std::vector<Launch>* cached_plan(KeyKind kk, bool has_vals, int m, int var
                                        uint32_t map_in, uint32_t map_out) {
   const Tuning tn = tuning_for(kk, has_vals, m);
   PlanKey key{int(kk), int(has_vals), m, variant, map_in, map_out, tn.t, tn.e1, tn.e2, tn.c2,
-              tn.w2 * 16 + tn.tma, tn.var[0] * 4 + tn.var[1] * 2 + tn.var[2]};
+              tn.w2 * 16 + tn.tma + tn.shfl * 256, tn.var[0] * 4 + tn.var[1] * 2 + tn.var[2]};
   std::lock_guard<std::mutex> lk(g_ctx.mu);
   auto it = g_ctx.plans.find(key);
   if (it != g_ctx.plans.end()) return &it->second;
@@ -155,6 +158,8 @@ int darm_sort_init(int device, size_t workspace_bytes) {
   for_each_tile_kernel_u32(set_smem_attr, st);
   for_each_tile_kernel_u64(set_smem_attr, st);
   for_each_tma_kernel_u32(set_smem_attr, st);
+  for_each_tile_shfl_kernel_u32(set_smem_attr, st);
+  for_each_pcm_kernel(set_smem_attr, st);
   for_each_window2_kernel(set_smem_attr, st);
   if (st[1] != 0) {
     fprintf(stderr, "darm: configuring shared memory failed: %s\n",
@@ -448,6 +453,62 @@ int darm_plan_info(int dtype, size_t n, int has_vals, int variant, int* passes, 
   if (passes) *passes = int(plan->size());
   if (launches) *launches = int(plan->size());
   if (tile) *tile = plan->empty() ? 0 : int(1u << plan->front().P.b);
+  return DARM_OK;
+}
+
+int darm_plan_describe(int dtype, size_t n, int has_vals, int variant, char* buf, size_t cap) {
+  if (!g_ctx.inited) return DARM_ERR_NOT_INIT;
+  if (dtype < DARM_U32 || dtype > DARM_U64 || !buf || cap == 0) return DARM_ERR_INVALID_ARG;
+  if (n < 2 || (n & (n - 1)) != 0) return DARM_ERR_NOT_POW2;
+  const KeyKind kk = dtype == DARM_U64 ? KEY_U64 : KEY_U32;
+  const std::vector<Launch>* plan = cached_plan(kk, has_vals != 0, log2_exact(n), variant, 0, 0);
+  if (!plan) return DARM_ERR_INVALID_ARG;
+  const std::string d = describe(*plan);
+  const size_t k = std::min(d.size(), cap - 1);
+  std::memcpy(buf, d.data(), k);
+  buf[k] = '\0';
+  return DARM_OK;
+}
+
+int darm_plan_dump(int dtype, size_t n, int has_vals, int variant, const int32_t* tuning,
+                   size_t smem_limit, int32_t* out, int cap, int* count) {
+  if (dtype < DARM_U32 || dtype > DARM_U64) return DARM_ERR_INVALID_ARG;
+  if (variant < DARM_DIVERGENT || variant > DARM_AUTO || !count) return DARM_ERR_INVALID_ARG;
+  if (n < 2 || (n & (n - 1)) != 0 || n > (size_t(1) << 31)) return DARM_ERR_NOT_POW2;
+  const KeyKind kk = dtype == DARM_U64 ? KEY_U64 : KEY_U32;
+  const bool hv = has_vals != 0;
+  const int m = log2_exact(n);
+  Tuning tn = tuning_for(kk, hv, m);
+  if (tuning) {
+    tn.t = tuning[0];
+    tn.e1 = tuning[1];
+    tn.e2 = tuning[2];
+    tn.c2 = tuning[3];
+    tn.w2 = tuning[4];
+    tn.tma = tuning[5];
+    tn.shfl = tuning[6];
+  }
+  if (smem_limit == 0) smem_limit = g_ctx.inited ? g_ctx.smem_limit : size_t(232448 - 64);
+  const uint32_t map = dtype == DARM_F32 ? kMapF32 : 0u;
+  std::vector<Launch> plan;
+  if (!plan_array(plan, kk, hv, m, tn, variant, map, map, smem_limit)) return DARM_ERR_INVALID_ARG;
+  std::vector<int32_t> v;
+  for (const Launch& L : plan) {
+    const int32_t head[] = {int32_t(L.kind), L.fixed, L.tma, L.win1, L.win2, L.shfl, L.loge,
+                            L.variant, int32_t(L.grid), int32_t(L.threads), int32_t(L.smem),
+                            int32_t(L.P.b), int32_t(L.P.c), int32_t(L.P.w0), int32_t(L.P.s),
+                            int32_t(L.P.log2cap), int32_t(L.P.nrounds), int32_t(L.P.nblocks),
+                            int32_t(L.P.map_in), int32_t(L.P.map_out)};
+    v.insert(v.end(), head, head + 20);
+    for (uint32_t r = 0; r < L.P.nrounds; ++r) {
+      const Round& R = L.P.rounds[r];
+      const int32_t row[] = {R.kind, R.p, R.a, R.cnt, R.src, R.dst, R.lanediv};
+      v.insert(v.end(), row, row + 7);
+    }
+  }
+  *count = int(v.size());
+  if (!out || cap < int(v.size())) return DARM_ERR_INVALID_ARG;
+  std::copy(v.begin(), v.end(), out);
   return DARM_OK;
 }
 

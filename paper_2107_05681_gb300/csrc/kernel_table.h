@@ -21,6 +21,10 @@ KernelEntry kernel_u64(bool has_vals, int loge, int var);
 KernelEntry tile_kernel_u32(bool has_vals, int loge, int logt, int var, bool merge);
 KernelEntry tile_kernel_u64(bool has_vals, int loge, int logt, int var, bool merge);
 
+// Tile passes whose stages 2E .. 32E run across lanes with shuffles
+// (tile_shfl_kernel.cuh), whole arrays only; {nullptr, 0} when not built.
+KernelEntry tile_shfl_kernel_u32(bool has_vals, int loge, int logt, int var);
+
 // Persistent merge kernels that prefetch tiles with bulk copies
 // (tma_merge.cuh); smem_bytes receives the dynamic shared memory they need.
 KernelEntry tma_merge_kernel_u32(bool has_vals, int loge, int logt, int ns, int var,
@@ -41,6 +45,7 @@ void for_each_kernel_u64(void (*fn)(const void*, void*), void* ctx);
 void for_each_tile_kernel_u32(void (*fn)(const void*, void*), void* ctx);
 void for_each_tile_kernel_u64(void (*fn)(const void*, void*), void* ctx);
 void for_each_tma_kernel_u32(void (*fn)(const void*, void*), void* ctx);
+void for_each_tile_shfl_kernel_u32(void (*fn)(const void*, void*), void* ctx);
 void for_each_window2_kernel(void (*fn)(const void*, void*), void* ctx);
 
 }  // namespace darm

@@ -96,6 +96,10 @@ struct SegBlock {
                        // sentinels beyond len
 };
 
+// The table sizes the C ABI documents for the no-allocation segmented sort.
+static_assert(sizeof(SegSlot) == 16, "SegSlot is 16 bytes");
+static_assert(sizeof(SegBlock) == 12, "SegBlock is 12 bytes");
+
 constexpr uint32_t kStatusSentinelCollision = 8u;  // == DARM_ERR_SENTINEL_COLLISION
 
 struct PassParams {
@@ -164,10 +168,26 @@ __device__ __forceinline__ void cswap(bool s, K& a, K& b, uint32_t& va, uint32_t
   }
 }
 
-// The two sides of Fig. 1's direction branch.
+__device__ __forceinline__ uint32_t kmin(uint32_t a, uint32_t b) { return umin(a, b); }
+__device__ __forceinline__ uint32_t kmax(uint32_t a, uint32_t b) { return umax(a, b); }
+__device__ __forceinline__ uint64_t kmin(uint64_t a, uint64_t b) { return ullmin(a, b); }
+__device__ __forceinline__ uint64_t kmax(uint64_t a, uint64_t b) { return ullmax(a, b); }
+
+// The two sides of Fig. 1's direction branch.  Without a payload the strict
+// swap leaves (min, max) ascending and (max, min) descending - equal keys
+// are indistinguishable - so the side is one unsigned min and one max (two
+// instructions instead of a compare and two selects).  With a payload the
+// swap predicate key[l] < key[i] (or >) moves the payload with its key.
 template <typename K, bool V, bool ASC>
 __device__ __forceinline__ void ce_side(K& a, K& b, uint32_t& va, uint32_t& vb) {
-  cswap<K, V>(ASC ? (b < a) : (b > a), a, b, va, vb);
+  if constexpr (!V) {
+    const K lo = kmin(a, b);
+    const K hi = kmax(a, b);
+    a = ASC ? lo : hi;
+    b = ASC ? hi : lo;
+  } else {
+    cswap<K, V>(ASC ? (b < a) : (b > a), a, b, va, vb);
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -10,6 +10,7 @@
 namespace darm {
 
 int fixed_schedule_rounds(int logt, int loge, bool merge, SRound* out, int cap);
+int shfl_schedule_rounds(int logt, int loge, SRound* out, int cap);
 
 // A compile-time-schedule kernel is used only if one was built for this
 // (key, payload, E, T) and its schedule equals the planner's round list.
@@ -32,6 +33,23 @@ static bool has_fixed(KeyKind kk, bool has_vals, int loge, int logt) {
   return true;
 }
 
+// A shuffle-stage tile kernel is used only if one was built for this shape
+// and its compile-time schedule equals the planner's round list.
+static bool has_shfl(KeyKind kk, bool has_vals, int loge, int logt) {
+  if (kk != KEY_U32 || tile_shfl_kernel_u32(has_vals, loge, logt, 1).fn == nullptr) return false;
+  SRound sr[kMaxRounds];
+  const int n = shfl_schedule_rounds(logt, loge, sr, kMaxRounds);
+  const std::vector<Round> rs = tile_rounds_shfl(logt, loge);
+  if (n != int(rs.size())) return false;
+  for (int i = 0; i < n; ++i) {
+    const Round& r = rs[i];
+    if (sr[i].kind != r.kind || sr[i].p != r.p || sr[i].a != r.a || sr[i].cnt != r.cnt ||
+        sr[i].src != r.src || sr[i].dst != r.dst)
+      return false;
+  }
+  return true;
+}
+
 int g_sms_for_plans = 152;
 
 static int max_threads(KeyKind kk, bool has_vals, int loge) {
@@ -49,6 +67,7 @@ Tuning default_tuning(KeyKind kk, bool has_vals) {
     tn.c2 = 8;
     tn.w2 = 2;
     tn.tma = 2;  // two tiles stream in while one is merged (200 KiB per SM)
+    tn.shfl = 1;  // 2^26 float keys: tile pass 0.686 -> 0.639 ms
   } else if (words == 2) {
     tn.t = 12;  // 4 Ki (key, payload) pairs = 36 KiB with padding: four CTAs per SM
     tn.e1 = 4;
@@ -56,6 +75,7 @@ Tuning default_tuning(KeyKind kk, bool has_vals) {
     tn.c2 = 8;
     tn.w2 = 2;
     tn.tma = 1;
+    tn.shfl = 1;  // 2^24 key-value pairs: tile pass 0.335 -> 0.267 ms
   } else {
     tn.t = 12;  // 4 Ki elements of 12 bytes = 48 KiB
     tn.e1 = 3;
@@ -111,6 +131,36 @@ std::vector<Round> tile_rounds(int t, int e) {
   a.dst = (t == e) ? LOC_GLOBAL : LOC_SMEM;
   rs.push_back(a);
   for (int p = e + 1; p <= t; ++p) {
+    const int nw = (p + e - 1) / e;
+    for (int i = nw - 1; i >= 0; --i) {
+      const int lo = i * e;
+      const int hi = std::min((i + 1) * e, p) - 1;
+      Round r{};
+      r.kind = RK_WINDOW;
+      r.p = uint8_t(p);
+      r.a = uint8_t(hi - e + 1);
+      r.cnt = uint8_t(hi - lo + 1);
+      r.src = LOC_SMEM;
+      r.dst = LOC_SMEM;
+      rs.push_back(r);
+    }
+  }
+  rs.back().dst = LOC_GLOBAL;
+  return rs;
+}
+
+std::vector<Round> tile_rounds_shfl(int t, int e) {
+  const int last_shfl = e + std::min(5, t - e);
+  std::vector<Round> rs;
+  Round a{};
+  a.kind = RK_PHASE_A;
+  a.p = uint8_t(last_shfl);  // Phase A runs stages up to 2^last_shfl
+  a.a = 0;
+  a.cnt = uint8_t(e);
+  a.src = LOC_GLOBAL;
+  a.dst = (t == last_shfl) ? LOC_GLOBAL : LOC_SMEM;
+  rs.push_back(a);
+  for (int p = last_shfl + 1; p <= t; ++p) {
     const int nw = (p + e - 1) / e;
     for (int i = nw - 1; i >= 0; --i) {
       const int lo = i * e;
@@ -194,11 +244,12 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
     Launch L{};
     L.kind = PASS_TILE;
     L.fixed = has_fixed(kk, has_vals, e1, t);
+    L.shfl = tn.shfl != 0 && has_shfl(kk, has_vals, e1, t);
     L.loge = e1;
     L.variant = pick_var(variant, tn, PASS_TILE);
     L.grid = uint32_t(1u << (m - t));
     L.threads = 1u << (t - e1);
-    std::vector<Round> rs = tile_rounds(t, e1);
+    std::vector<Round> rs = L.shfl ? tile_rounds_shfl(t, e1) : tile_rounds(t, e1);
     mark_lanes(rs, e1, t, t - e1);
     L.smem = uses_smem(rs) ? tile_smem : 0;
     L.P.b = uint32_t(t);
@@ -338,7 +389,7 @@ std::string describe(const std::vector<Launch>& plan) {
   std::ostringstream os;
   static const char* names[] = {"tile", "window", "merge"};
   for (const Launch& L : plan) {
-    os << names[L.kind] << (L.fixed ? "*" : "") << " E=" << (1 << L.loge) << " var=" << L.variant << " grid=" << L.grid
+    os << names[L.kind] << (L.fixed ? "*" : "") << (L.shfl ? "~" : "") << " E=" << (1 << L.loge) << " var=" << L.variant << " grid=" << L.grid
        << " threads=" << L.threads << " smem=" << L.smem << " b=" << L.P.b << " c=" << L.P.c
        << " w0=" << L.P.w0 << " rounds=" << L.P.nrounds << "\n";
   }

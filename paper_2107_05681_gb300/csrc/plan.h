@@ -35,6 +35,8 @@ struct Tuning {
               // shared-memory exchange, 2*e2 layers per HBM sweep)
   int tma = 0; // merge passes of single arrays prefetch tiles with bulk copies
                // into this many staging buffers (0: plain merge kernel)
+  int shfl = 0; // tile passes of single arrays run stages 2E .. 32E across
+                // lanes with shuffles (tile_shfl_kernel.cuh) where built
   int var[3]; // variant per pass kind (used when DARM_AUTO is requested)
 };
 
@@ -48,6 +50,7 @@ struct Launch {
                // staging buffers (tma_merge.cuh); 0: plain merge kernel
   bool win2;   // two-window pass with a compile-time shape (window2_kernel.cuh)
   bool win1;   // one-window pass with a compile-time shape (window1_kernel.cuh)
+  bool shfl;   // tile pass with shuffle stages (tile_shfl_kernel.cuh)
   int loge;
   int variant;
   uint32_t grid;
@@ -71,6 +74,9 @@ bool fit_tuning(Tuning& tn, KeyKind kk, bool has_vals, int m, size_t smem_limit)
 // t-1 .. 0 of one stage p > t).
 std::vector<Round> tile_rounds(int t, int e);
 std::vector<Round> merge_rounds(int t, int e, int p);
+// Rounds of a tile pass whose first round also runs stages E+1 .. E+S
+// (S = min(5, t - e)) across lanes with shuffles.
+std::vector<Round> tile_rounds_shfl(int t, int e);
 
 // Whole-array plan.  variant: 0/1 force divergent/melded everywhere, 2 uses
 // tn.var per pass kind.  map_in/map_out: key transforms of the first load and

@@ -118,6 +118,19 @@ int darm_autotune(int dtype, size_t n, int has_vals, const char* db_path) {
               best = tn;
             }
           }
+  // the tile pass with shuffle stages instead of shared-memory rounds for
+  // strides E .. 16E, where one is built for the chosen shape
+  {
+    Tuning tn = best;
+    tn.shfl = 1;
+    std::vector<Launch> plan;
+    float kind[3], tot;
+    if (plan_array(plan, kk, hv, m, tn, DARM_AUTO, 0, 0, g_ctx.smem_limit) && plan[0].shfl &&
+        time_plan(plan, kk, keys, vals, kbytes / 4, s, 3, kind, &tot) && tot < best_ms) {
+      best_ms = tot;
+      best = tn;
+    }
+  }
   // per pass kind: divergent or melded
   float kind_of[2][3];
   for (int v = 0; v < 2; ++v) {
@@ -141,11 +154,19 @@ int darm_autotune(int dtype, size_t n, int has_vals, const char* db_path) {
   if (db_path) {
     FILE* f = fopen(db_path, "a");
     if (!f) return DARM_ERR_INVALID_ARG;
-    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %.6f\n", int(kk), int(hv), m, best.t, best.e1,
-            best.e2, best.c2, best.w2, best.tma, best.var[0], best.var[1], best.var[2],
-            double(best_ms));
+    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %.6f %d\n", int(kk), int(hv), m, best.t,
+            best.e1, best.e2, best.c2, best.w2, best.tma, best.var[0], best.var[1], best.var[2],
+            double(best_ms), best.shfl);
     fclose(f);
   }
+  return DARM_OK;
+}
+
+int darm_reset_tunings(void) {
+  if (!g_ctx.inited) return DARM_ERR_NOT_INIT;
+  std::lock_guard<std::mutex> lk(g_ctx.mu);
+  g_ctx.tuned.clear();
+  g_ctx.plans.clear();
   return DARM_OK;
 }
 
@@ -155,12 +176,18 @@ int darm_load_tune_db(const char* db_path) {
   FILE* f = fopen(db_path, "r");
   if (!f) return DARM_ERR_NOT_FOUND;
   int kk, hv, m;
-  Tuning tn;
   double ms;
   int loaded = 0;
+  char line[512];
   std::lock_guard<std::mutex> lk(g_ctx.mu);
-  while (fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %lf", &kk, &hv, &m, &tn.t, &tn.e1,
-                &tn.e2, &tn.c2, &tn.w2, &tn.tma, &tn.var[0], &tn.var[1], &tn.var[2], &ms) == 13) {
+  // one tuning per line: 13 fields, and a 14th (shuffle stages) when present
+  while (fgets(line, sizeof line, f)) {
+    Tuning tn;
+    const int got = sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d %lf %d", &kk, &hv, &m, &tn.t,
+                           &tn.e1, &tn.e2, &tn.c2, &tn.w2, &tn.tma, &tn.var[0], &tn.var[1],
+                           &tn.var[2], &ms, &tn.shfl);
+    if (got < 13) continue;
+    if (got == 13) tn.shfl = 0;
     if (kk < 0 || kk > 1 || m < 0 || m > 31) continue;
     g_ctx.tuned[std::make_tuple(kk, hv, m)] = tn;  // m == 0: a batch tuning
     ++loaded;

@@ -1,0 +1,103 @@
+"""Bounds and network checks of every whole-array plan, on the CPU.
+
+The planner's launch lists (darm_plan_dump, no device needed) are replayed
+through the kernels' index arithmetic (tests/plan_emulator.py): each round
+must touch every element exactly once, stay inside the array and inside the
+launch's shared memory, pair registers whose elements differ in one index
+bit, and the whole plan must run Fig. 1's layers in Fig. 1's order.  This
+stands in for a bounds-checking tool on the GPU."""
+import numpy as np
+import pytest
+
+import paper_2107_05681_gb300 as darm
+from tests import plan_emulator as em
+
+KINDS = [(darm.U32, 4, False), (darm.U32, 4, True), (darm.F32, 4, False), (darm.U64, 8, False),
+         (darm.U64, 8, True)]
+
+
+@pytest.mark.parametrize("dtype,kb,hv", KINDS)
+def test_default_plans_every_size_enumerated(dtype, kb, hv):
+    for m in range(1, 19):
+        n = 1 << m
+        for variant in ("melded", "divergent"):
+            plan = darm.plan_dump(dtype, n, hv, variant)
+            em.check_plan(plan, n, kb, hv, full=True)
+
+
+@pytest.mark.parametrize("dtype,kb,hv,m", [(darm.U32, 4, True, 24), (darm.F32, 4, False, 26),
+                                           (darm.U32, 4, False, 28), (darm.U64, 8, True, 24),
+                                           (darm.U32, 4, True, 31)])
+def test_full_size_plans_bit_linear(dtype, kb, hv, m):
+    """The benchmark's workloads (2^24 key-value pairs, 2^26 float keys) and
+    the largest arrays the library accepts."""
+    plan = darm.plan_dump(dtype, 1 << m, hv, "melded")
+    em.check_plan(plan, 1 << m, kb, hv, full=False, rng=np.random.default_rng(m))
+
+
+def _tuner_candidates(hv):
+    base_t, base_e1 = (12, 4) if hv else (14, 5)
+    for t in (base_t - 1, base_t, base_t + 1):
+        for e1 in (base_e1 - 1, base_e1):
+            for e2 in (3, 4, 5):
+                for w2 in (1, 2):
+                    for tma in (0, 1, 2):
+                        for shfl in (0, 1):
+                            yield (t, e1, e2, 8, w2, tma, shfl)
+
+
+@pytest.mark.parametrize("hv", [False, True])
+@pytest.mark.parametrize("part", range(4))
+def test_tuner_candidate_plans(hv, part):
+    """Tunings the whole-array autotuner tries (and the shuffle-stage tile
+    pass on and off) on an array of 2^16 elements: one candidate in four,
+    the choice rotating through every block of 16 candidates so that each
+    tuning field takes all its values, spread over four cases."""
+    n = 1 << 16
+    checked = 0
+    for i, tn in enumerate(_tuner_candidates(hv)):
+        if i % 16 != part * 4 + (i // 16) % 4:
+            continue
+        try:
+            plan = darm.plan_dump(darm.U32, n, hv, "melded", tuning=tn)
+        except darm.DarmError:
+            continue  # no valid plan for this tuning: the tuner skips it too
+        em.check_plan(plan, n, 4, hv, full=True)
+        checked += 1
+    assert checked >= 8
+
+
+def test_plans_of_each_kernel_kind_are_covered():
+    kinds = set()
+    for dtype, kb, hv in KINDS:
+        for m in (12, 16, 18, 24, 26):
+            for L in darm.plan_dump(dtype, 1 << m, hv, "melded"):
+                kinds.add(em.Kernel(L, kb, hv).kind)
+    for tn in ((14, 5, 5, 8, 1, 0, 0), (13, 5, 4, 8, 2, 0, 0)):
+        for L in darm.plan_dump(darm.U32, 1 << 18, False, "melded", tuning=tn):
+            kinds.add(em.Kernel(L, 4, False).kind)
+    assert {"tile_shfl", "tile_fixed", "tma_merge", "window1", "window2"} <= kinds, kinds
+
+
+@pytest.mark.parametrize("mutation", ["cnt", "a", "w0", "grid", "p"])
+def test_a_planted_off_by_one_is_caught(mutation):
+    """An off-by-one planted in a plan (one field of one launch) fails the
+    replay."""
+    n = 1 << 16
+    plan = darm.plan_dump(darm.U32, n, True, "melded")
+    em.check_plan(plan, n, 4, True, full=True)
+    bad = [dict(L, rounds=[dict(R) for R in L["rounds"]]) for L in plan]
+    win = next(L for L in bad if L["kind"] == em.WINDOW)
+    merge = next(L for L in bad if L["kind"] == em.MERGE)
+    if mutation == "cnt":
+        merge["rounds"][-1]["cnt"] -= 1
+    elif mutation == "a":
+        merge["rounds"][1]["a"] += 1
+    elif mutation == "w0":
+        win["w0"] += 1
+    elif mutation == "grid":
+        win["grid"] -= 1
+    else:
+        merge["rounds"][0]["p"] -= 1
+    with pytest.raises(AssertionError):
+        em.check_plan(bad, n, 4, True, full=True)
