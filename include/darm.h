@@ -124,6 +124,42 @@ int darm_bitonic_sort_u64(uint64_t* keys, uint32_t* vals, size_t n, int dir,
 int darm_bitonic_sort_host(void* keys, uint32_t* vals, size_t n, int dtype,
                            int dir, int variant);
 
+/* ---- one array split into shards (one per process or device) -------------- */
+
+/* The network of one array of nshards * n elements whose shard `shard`
+ * (elements shard*n .. shard*n + n - 1) lives in keys/vals (DEVICE, n a power
+ * of two, nshards a power of two, n * nshards <= 2^31).  Composed as:
+ *   darm_bitonic_sort_shard;
+ *   for every stage k = 2n, 4n, .. nshards*n (log2k = log2 of k):
+ *     for every layer j = k/2 .. n (log2j): exchange the shard with shard
+ *       shard ^ (j / n) (the caller moves the peer's copy into peer_keys /
+ *       peer_vals on this device) and call darm_bitonic_exchange;
+ *     darm_bitonic_merge_shard(log2k).
+ * Every comparator is the whole array's (Fig. 1), so the shards end holding
+ * exactly the whole-array sort.  Between the first call and the final
+ * stage's merge the keys are in the network's internal form (float keys as
+ * totalOrder words, descending sorts complemented); the final merge restores
+ * them.  With nshards = 1, darm_bitonic_sort_shard alone sorts the array.
+ * Errors: DARM_ERR_NOT_POW2, DARM_ERR_INVALID_ARG (shard >= nshards,
+ * misaligned or NULL buffers, a layer outside the schedule, a shard within
+ * one tile for darm_bitonic_merge_shard), DARM_ERR_CUDA. */
+int darm_bitonic_sort_shard(void* keys, uint32_t* vals, size_t n, int dtype, size_t shard,
+                            size_t nshards, int dir, int variant, void* stream);
+
+/* Layer j = 2^log2j (n <= j < k) of stage k = 2^log2k: element i of this
+ * shard and element i of shard shard ^ (j / n) (peer_keys / peer_vals, the
+ * peer's values before this layer) form one comparator; this shard keeps its
+ * side of the pair.  One direction for the whole shard, so there is no
+ * divergent and melded form. */
+int darm_bitonic_exchange(void* keys, uint32_t* vals, const void* peer_keys,
+                          const uint32_t* peer_vals, size_t n, int dtype, size_t shard,
+                          size_t nshards, int log2k, int log2j, int dir, void* stream);
+
+/* Layers j = n/2 .. 1 of stage k = 2^log2k (k > n) on this shard (n must
+ * exceed one tile of the plan). */
+int darm_bitonic_merge_shard(void* keys, uint32_t* vals, size_t n, int dtype, size_t shard,
+                             size_t nshards, int log2k, int dir, int variant, void* stream);
+
 /* ---- batched segmented sort ------------------------------------------ */
 
 /* Sort num_segs independent segments in one batched launch sequence: the

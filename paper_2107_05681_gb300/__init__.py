@@ -63,6 +63,10 @@ _sig = {
     "darm_oddeven_sort_buckets": ([_vp, _vp, _sz, _sz, _i32, _vp], _i32),
     "darm_sb_run": ([_i32, _vp, _sz, _i32, _i32, _i32, _vp], _i32),
     "darm_pcm_sort": ([_vp, _vp, _sz, _sz, _vp, _vp, _i32, _vp], _i32),
+    "darm_bitonic_sort_shard": ([_vp, _vp, _sz, _i32, _sz, _sz, _i32, _i32, _vp], _i32),
+    "darm_bitonic_exchange": ([_vp, _vp, _vp, _vp, _sz, _i32, _sz, _sz, _i32, _i32, _i32, _vp],
+                              _i32),
+    "darm_bitonic_merge_shard": ([_vp, _vp, _sz, _i32, _sz, _sz, _i32, _i32, _i32, _vp], _i32),
     "darm_meld_mp_block": ([_vp, _i32, _vp, _i32], ctypes.c_double),
     "darm_meld_mp_subgraph": ([_vp, _vp, _vp, _vp, _i32], ctypes.c_double),
     "darm_meld_align": ([_vp, _i32, _vp, _i32, ctypes.c_double, _vp, _vp], _i32),
@@ -348,6 +352,56 @@ def pcm_sort(keys, vals=None, bucket: int = 4096, scratch_keys=None, scratch_val
                            ctypes.c_void_p(scratch_keys.data_ptr()), svp, _variant(variant),
                            _stream_handle(stream))
     _check(rc, "darm_pcm_sort")
+
+
+def _key_dtype_code(keys):
+    import torch
+    codes = {torch.uint32: U32, torch.float32: F32, torch.uint64: U64}
+    if keys.dtype not in codes or not keys.is_cuda or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous uint32, float32 or uint64 CUDA tensor")
+    return codes[keys.dtype]
+
+
+def _vals_ptr(keys, vals):
+    import torch
+    if vals is None:
+        return None
+    if vals.dtype != torch.uint32 or vals.shape != keys.shape or not vals.is_contiguous():
+        raise ValueError("vals must be a contiguous uint32 CUDA tensor shaped like keys")
+    return ctypes.c_void_p(vals.data_ptr())
+
+
+def sort_shard(keys, vals, shard: int, nshards: int, descending=False, variant="melded",
+               stream=None) -> None:
+    """Stages 2 .. n of the network of an array of nshards shards, on shard
+    `shard` (keys/vals: that shard, on this device)."""
+    rc = lib.darm_bitonic_sort_shard(ctypes.c_void_p(keys.data_ptr()), _vals_ptr(keys, vals),
+                                     keys.numel(), _key_dtype_code(keys), int(shard),
+                                     int(nshards), DESC if descending else ASC,
+                                     _variant(variant), _stream_handle(stream))
+    _check(rc, "darm_bitonic_sort_shard")
+
+
+def exchange_shard(keys, vals, peer_keys, peer_vals, shard: int, nshards: int, log2k: int,
+                   log2j: int, descending=False, stream=None) -> None:
+    """Layer 2^log2j of stage 2^log2k against the peer shard's copy."""
+    rc = lib.darm_bitonic_exchange(
+        ctypes.c_void_p(keys.data_ptr()), _vals_ptr(keys, vals),
+        ctypes.c_void_p(peer_keys.data_ptr()),
+        None if peer_vals is None else ctypes.c_void_p(peer_vals.data_ptr()), keys.numel(),
+        _key_dtype_code(keys), int(shard), int(nshards), int(log2k), int(log2j),
+        DESC if descending else ASC, _stream_handle(stream))
+    _check(rc, "darm_bitonic_exchange")
+
+
+def merge_shard(keys, vals, shard: int, nshards: int, log2k: int, descending=False,
+                variant="melded", stream=None) -> None:
+    """Layers n/2 .. 1 of stage 2^log2k on this shard."""
+    rc = lib.darm_bitonic_merge_shard(ctypes.c_void_p(keys.data_ptr()), _vals_ptr(keys, vals),
+                                      keys.numel(), _key_dtype_code(keys), int(shard),
+                                      int(nshards), int(log2k), DESC if descending else ASC,
+                                      _variant(variant), _stream_handle(stream))
+    _check(rc, "darm_bitonic_merge_shard")
 
 
 def sort_host(keys, vals=None, descending: bool = False, variant="melded") -> None:

@@ -7,7 +7,9 @@ VARIANT: melded | divergent.  WORKLOAD: cfg1 (4096 uint32 keys, one block),
 oem4096 (the same keys through the single-block odd-even merge sort network),
 oem26 (2^26 uint32 keys through that network in buckets of 4096, one block each),
 SB1 | SB4 | SB1-R | SB4-R (the synthetic divergent kernels, 1216 blocks),
-kv24 (2^24 uint32 key-value pairs), f32 (2^26 float32 keys).
+kv24 (2^24 uint32 key-value pairs), f32 (2^26 float32 keys),
+pcm26 (PCM of 2^26 uint32 keys in buckets of 4096: one bucket-sort launch and
+105 merge-split layer launches per sort, then one gather launch).
 """
 import sys
 
@@ -34,6 +36,15 @@ def main(variant="melded", workload="kv24"):
         for _ in range(2):
             K2 = K.clone()
             darm.oddeven_sort_buckets(K2, bucket=4096, variant=variant)
+        torch.cuda.synchronize()
+        print("ok", darm.launch_count())
+        return
+    if workload == "pcm26":
+        K = torch.from_numpy(synth.uniform_u32(0xDA2C0008, 1 << 26)).cuda()
+        S = torch.empty_like(K)
+        for _ in range(2):
+            K2 = K.clone()
+            darm.pcm_sort(K2, bucket=4096, scratch_keys=S, variant=variant)
         torch.cuda.synchronize()
         print("ok", darm.launch_count())
         return
