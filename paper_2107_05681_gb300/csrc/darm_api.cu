@@ -84,7 +84,8 @@ const std::vector<Launch>* cached_plan(KeyKind kk, bool has_vals, int m, int var
                                        uint32_t map_in, uint32_t map_out) {
   const Tuning tn = tuning_for(kk, has_vals, m);
   PlanKey key{int(kk), int(has_vals), m, variant, map_in, map_out, tn.t, tn.e1, tn.e2, tn.c2,
-              tn.w2 * 16 + tn.tma + tn.shfl * 256, tn.var[0] * 4 + tn.var[1] * 2 + tn.var[2]};
+              tn.w2 * 16 + tn.tma + tn.shfl * 256 + tn.em * 1024,
+              tn.var[0] * 4 + tn.var[1] * 2 + tn.var[2]};
   std::lock_guard<std::mutex> lk(g_ctx.mu);
   auto it = g_ctx.plans.find(key);
   if (it != g_ctx.plans.end()) return &it->second;

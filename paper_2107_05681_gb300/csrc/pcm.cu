@@ -221,6 +221,125 @@ __global__ void __launch_bounds__(kPcmThreads) darm_pcm_layer_kernel(const PcmLa
   }
 }
 
+// Buckets of 256 keys or more: 2S/16 threads (at least 32), 16 outputs each.
+// Same algorithm as darm_pcm_layer_kernel with less bookkeeping: the
+// buckets' locations are summed by the lanes of each warp (one stage per
+// lane) instead of a serial loop in every thread; a side's next key is
+// read without a bound check (the slot after A is B's first, the slot after
+// B is the region's spare word, and neither is used once that side is
+// exhausted); and a thread's 16 outputs are contiguous slots, so their
+// addresses are immediates.
+constexpr uint32_t kPcmQ = 16;
+
+__device__ __forceinline__ uint32_t pcm_parity_warp(uint32_t x, uint32_t s, uint32_t t) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t n = 0;
+  if (lane < s)
+    n = pcm_stage_parts(x, lane, 0);
+  else if (lane == s)
+    n = pcm_stage_parts(x, s, t + 1);
+  return __reduce_add_sync(0xFFFFFFFFu, n) & 1u;
+}
+
+template <bool V, int VAR>
+__global__ void __launch_bounds__(kPcmThreads) darm_pcm_layer16_kernel(const PcmLayer L) {
+  extern __shared__ __align__(16) uint32_t pcm_smem[];
+  const uint32_t S = L.S;
+  const uint32_t R = padded_words(2 * S);
+  uint32_t* sAB = pcm_smem;
+  uint32_t* sOut = pcm_smem + R;
+  uint32_t* sVAB = pcm_smem + 2 * R;
+  uint32_t* sVOut = pcm_smem + 3 * R;
+
+  const uint32_t c = blockIdx.x;
+  const uint32_t p = 1u << L.s, k = 1u << L.t;
+  uint32_t x;
+  if (L.t == L.s) {
+    x = ((c >> L.s) << (L.s + 1)) | (c & (p - 1u));
+  } else {
+    const uint32_t per = p - k;
+    const uint32_t q = c / per, r = c - q * per;
+    x = (q << (L.s + 1)) + k + ((r >> L.t) << (L.t + 1)) + (r & (k - 1u));
+  }
+  const uint32_t y = x + k;
+  const uint32_t la = pcm_parity_warp(x, L.s, L.t);
+  const uint32_t lb = pcm_parity_warp(y, L.s, L.t);
+  const uint32_t tid = threadIdx.x, nt = blockDim.x;
+  {
+    const uint4* gA = reinterpret_cast<const uint4*>(kbuf(L, la) + size_t(x) * S);
+    const uint4* gB = reinterpret_cast<const uint4*>(kbuf(L, lb) + size_t(y) * S);
+    const uint4* vA = V ? reinterpret_cast<const uint4*>(vbuf(L, la) + size_t(x) * S) : nullptr;
+    const uint4* vB = V ? reinterpret_cast<const uint4*>(vbuf(L, lb) + size_t(y) * S) : nullptr;
+    for (uint32_t e = tid; e < S / 4; e += nt) {
+      const uint4 ka = __ldg(gA + e), kb = __ldg(gB + e);
+      put4(sAB, 4 * e, ka);
+      put4(sAB, S + 4 * e, kb);
+      if (V) {
+        put4(sVAB, 4 * e, __ldg(vA + e));
+        put4(sVAB, S + 4 * e, __ldg(vB + e));
+      }
+    }
+  }
+  __syncthreads();
+
+  const uint32_t d = tid * kPcmQ;
+  uint32_t lo = d > S ? d - S : 0u, hi = d < S ? d : S;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (sAB[pad(mid)] <= sAB[pad(S + (d - mid - 1))])
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  uint32_t i = lo, j = d - lo;  // next unread of A, of B
+  uint32_t a = sAB[pad(i)];      // read unconditionally: see above
+  uint32_t b = sAB[pad(S + j)];
+  const uint32_t po = pad(d);    // the 16 outputs are slots po .. po + 15
+#pragma unroll
+  for (uint32_t o = 0; o < kPcmQ; ++o) {
+    const bool ta = (j >= S) || (i < S && a <= b);
+    uint32_t key, val = 0;
+    if (VAR == kDivergent) {
+      if (ta) {
+        key = a;
+        if (V) val = sVAB[pad(i)];
+        ++i;
+        a = sAB[pad(i)];
+      } else {
+        key = b;
+        if (V) val = sVAB[pad(S + j)];
+        ++j;
+        b = sAB[pad(S + j)];
+      }
+    } else {
+      key = ta ? a : b;
+      const uint32_t slot = ta ? i : S + j;
+      if (V) val = sVAB[pad(slot)];
+      i += ta ? 1u : 0u;
+      j += ta ? 0u : 1u;
+      const uint32_t fresh = sAB[pad(slot + 1)];
+      a = ta ? fresh : a;
+      b = ta ? b : fresh;
+    }
+    sOut[po + o] = key;
+    if (V) sVOut[po + o] = val;
+  }
+  __syncthreads();
+
+  uint4* oA = reinterpret_cast<uint4*>(kbuf(L, la ^ 1u) + size_t(x) * S);
+  uint4* oB = reinterpret_cast<uint4*>(kbuf(L, lb ^ 1u) + size_t(y) * S);
+  uint4* wA = V ? reinterpret_cast<uint4*>(vbuf(L, la ^ 1u) + size_t(x) * S) : nullptr;
+  uint4* wB = V ? reinterpret_cast<uint4*>(vbuf(L, lb ^ 1u) + size_t(y) * S) : nullptr;
+  for (uint32_t e = tid; e < S / 4; e += nt) {
+    oA[e] = get4(sOut, 4 * e);
+    oB[e] = get4(sOut, S + 4 * e);
+    if (V) {
+      wA[e] = get4(sVOut, 4 * e);
+      wB[e] = get4(sVOut, S + 4 * e);
+    }
+  }
+}
+
 // Buckets whose last merge-split left them in the scratch: copy them back.
 template <bool V>
 __global__ void __launch_bounds__(256) darm_pcm_gather_kernel(const PcmLayer L, uint32_t nstages) {
@@ -242,6 +361,10 @@ size_t pcm_smem_bytes(bool has_vals, uint32_t S) {
 }  // namespace
 
 void for_each_pcm_kernel(void (*fn)(const void*, void*), void* ctx) {
+  fn(reinterpret_cast<const void*>(&darm_pcm_layer16_kernel<false, 0>), ctx);
+  fn(reinterpret_cast<const void*>(&darm_pcm_layer16_kernel<false, 1>), ctx);
+  fn(reinterpret_cast<const void*>(&darm_pcm_layer16_kernel<true, 0>), ctx);
+  fn(reinterpret_cast<const void*>(&darm_pcm_layer16_kernel<true, 1>), ctx);
   fn(reinterpret_cast<const void*>(&darm_pcm_layer_kernel<false, 0>), ctx);
   fn(reinterpret_cast<const void*>(&darm_pcm_layer_kernel<false, 1>), ctx);
   fn(reinterpret_cast<const void*>(&darm_pcm_layer_kernel<true, 0>), ctx);
@@ -283,10 +406,16 @@ extern "C" int darm_pcm_sort(uint32_t* keys, uint32_t* vals, size_t n, size_t bu
   L.S = S;
   const uint32_t threads = uint32_t(std::max<size_t>(1, std::min<size_t>(kPcmThreads, 2 * S / kPcmPerThread)));
   const size_t smem = pcm_smem_bytes(hv, S);
-  const void* fn = hv ? (melded ? reinterpret_cast<const void*>(&darm_pcm_layer_kernel<true, 1>)
-                                : reinterpret_cast<const void*>(&darm_pcm_layer_kernel<true, 0>))
-                      : (melded ? reinterpret_cast<const void*>(&darm_pcm_layer_kernel<false, 1>)
-                                : reinterpret_cast<const void*>(&darm_pcm_layer_kernel<false, 0>));
+  const bool q16 = S >= 256;  // 2S/16 >= 32 threads: the warp-summing kernel
+  const void* fn =
+      q16 ? (hv ? (melded ? reinterpret_cast<const void*>(&darm_pcm_layer16_kernel<true, 1>)
+                          : reinterpret_cast<const void*>(&darm_pcm_layer16_kernel<true, 0>))
+                : (melded ? reinterpret_cast<const void*>(&darm_pcm_layer16_kernel<false, 1>)
+                          : reinterpret_cast<const void*>(&darm_pcm_layer16_kernel<false, 0>)))
+          : (hv ? (melded ? reinterpret_cast<const void*>(&darm_pcm_layer_kernel<true, 1>)
+                          : reinterpret_cast<const void*>(&darm_pcm_layer_kernel<true, 0>))
+                : (melded ? reinterpret_cast<const void*>(&darm_pcm_layer_kernel<false, 1>)
+                          : reinterpret_cast<const void*>(&darm_pcm_layer_kernel<false, 0>)));
   uint32_t nstages = 0;
   while ((size_t(1) << nstages) < nb) ++nstages;
   const uint32_t B = uint32_t(nb);

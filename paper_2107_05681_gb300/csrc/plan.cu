@@ -345,13 +345,19 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
     // merge pass: layers t-1 .. 0 inside each tile
     Launch L{};
     L.kind = PASS_MERGE;
-    L.fixed = has_fixed(kk, has_vals, e1, t);
-    L.loge = e1;
+    // merge passes may run their own elements per thread (more, smaller
+    // threads when the tile needs more resident warps)
+    int em = e1;
+    if (tn.em > 0 && tn.em <= 5 && tn.em <= t && (1 << (t - tn.em)) <= 1024 &&
+        merge_round_count(t, tn.em) <= kMaxRounds && has_fixed(kk, has_vals, tn.em, t))
+      em = tn.em;
+    L.fixed = has_fixed(kk, has_vals, em, t);
+    L.loge = em;
     L.variant = pick_var(variant, tn, PASS_MERGE);
     L.grid = uint32_t(1u << (m - t));
-    L.threads = 1u << (t - e1);
-    std::vector<Round> rs = merge_rounds(t, e1, p);
-    mark_lanes(rs, e1, t, t - e1);
+    L.threads = 1u << (t - em);
+    std::vector<Round> rs = merge_rounds(t, em, p);
+    mark_lanes(rs, em, t, t - em);
     L.smem = uses_smem(rs) ? tile_smem : 0;
     L.P.b = uint32_t(t);
     L.P.c = uint32_t(t);
@@ -365,13 +371,13 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
     // bulk copies while the current one is processed (one CTA per SM)
     size_t tma_smem = 0;
     if (kk == KEY_U32 && tn.tma &&
-        tma_merge_kernel_u32(has_vals, e1, t, tn.tma, L.variant, &tma_smem).fn != nullptr &&
+        tma_merge_kernel_u32(has_vals, em, t, tn.tma, L.variant, &tma_smem).fn != nullptr &&
         tma_smem <= smem_limit) {
       L.tma = tn.tma;
       L.smem = tma_smem;
       L.P.nblocks = L.grid;
       int per_sm = 1;
-      const void* tfn = tma_merge_kernel_u32(has_vals, e1, t, tn.tma, L.variant, nullptr).fn;
+      const void* tfn = tma_merge_kernel_u32(has_vals, em, t, tn.tma, L.variant, nullptr).fn;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tfn, int(L.threads), L.smem) !=
               cudaSuccess ||
           per_sm < 1) {

@@ -37,6 +37,7 @@ struct Tuning {
                // into this many staging buffers (0: plain merge kernel)
   int shfl = 0; // tile passes of single arrays run stages 2E .. 32E across
                 // lanes with shuffles (tile_shfl_kernel.cuh) where built
+  int em = 0;   // log2 elements per thread in merge passes (0: e1)
   int var[3]; // variant per pass kind (used when DARM_AUTO is requested)
 };
 

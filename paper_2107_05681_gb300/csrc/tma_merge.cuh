@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_ke
             kr[r] = stage_k[l];
             if (V) vr[r] = stage_v[l];
           }
-          window_side<K, V, LOGE, ASC>(kr, vr, R.cnt);
+          window_side<K, V, LOGE, ASC, true>(kr, vr, R.cnt);
           s_store<K, V, LOGE, A, false, true>(kr, vr, LAST, gk, gv, g_full, sk, sv, s_base, mout, K(0));
         };
         if (asc)
@@ -206,11 +206,11 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_ke
       } else {
         if (asc) {
           s_load<K, V, LOGE, A, false>(kr, vr, false, gk, gv, g_full, sk, sv, s_base, 0u, K(0));
-          window_side<K, V, LOGE, true>(kr, vr, R.cnt);
+          window_side<K, V, LOGE, true, true>(kr, vr, R.cnt);
           s_store<K, V, LOGE, A, false, true>(kr, vr, LAST, gk, gv, g_full, sk, sv, s_base, mout, K(0));
         } else {
           s_load<K, V, LOGE, A, true>(kr, vr, false, gk, gv, g_full, sk, sv, s_base, 0u, K(0));
-          window_side<K, V, LOGE, false>(kr, vr, R.cnt);
+          window_side<K, V, LOGE, false, true>(kr, vr, R.cnt);
           s_store<K, V, LOGE, A, true, true>(kr, vr, LAST, gk, gv, g_full, sk, sv, s_base, mout, K(0));
         }
         __syncthreads();

@@ -32,6 +32,7 @@ KernelEntry tma_merge_kernel_u32(bool has_vals, int loge, int logt, int ns, int 
   if (has_vals && loge == 4 && logt == 13) return mpick<true, 4, 13>(ns, var, smem_bytes);
   if (!has_vals && loge == 5 && logt == 13) return mpick<false, 5, 13>(ns, var, smem_bytes);
   if (!has_vals && loge == 5 && logt == 14) return mpick<false, 5, 14>(ns, var, smem_bytes);
+  if (!has_vals && loge == 4 && logt == 14) return mpick<false, 4, 14>(ns, var, smem_bytes);
   return KernelEntry{nullptr, 0};
 }
 
@@ -42,6 +43,7 @@ void for_each_tma_kernel_u32(void (*fn)(const void*, void*), void* ctx) {
       fn(tma_merge_kernel_u32(true, 4, 13, ns, var, nullptr).fn, ctx);
       fn(tma_merge_kernel_u32(false, 5, 13, ns, var, nullptr).fn, ctx);
       fn(tma_merge_kernel_u32(false, 5, 14, ns, var, nullptr).fn, ctx);
+      fn(tma_merge_kernel_u32(false, 4, 14, ns, var, nullptr).fn, ctx);
     }
 }
 

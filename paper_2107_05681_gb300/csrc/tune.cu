@@ -154,9 +154,9 @@ int darm_autotune(int dtype, size_t n, int has_vals, const char* db_path) {
   if (db_path) {
     FILE* f = fopen(db_path, "a");
     if (!f) return DARM_ERR_INVALID_ARG;
-    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %.6f %d\n", int(kk), int(hv), m, best.t,
+    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %.6f %d %d\n", int(kk), int(hv), m, best.t,
             best.e1, best.e2, best.c2, best.w2, best.tma, best.var[0], best.var[1], best.var[2],
-            double(best_ms), best.shfl);
+            double(best_ms), best.shfl, best.em);
     fclose(f);
   }
   return DARM_OK;
@@ -183,11 +183,12 @@ int darm_load_tune_db(const char* db_path) {
   // one tuning per line: 13 fields, and a 14th (shuffle stages) when present
   while (fgets(line, sizeof line, f)) {
     Tuning tn;
-    const int got = sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d %lf %d", &kk, &hv, &m, &tn.t,
-                           &tn.e1, &tn.e2, &tn.c2, &tn.w2, &tn.tma, &tn.var[0], &tn.var[1],
-                           &tn.var[2], &ms, &tn.shfl);
+    const int got = sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d %lf %d %d", &kk, &hv, &m,
+                           &tn.t, &tn.e1, &tn.e2, &tn.c2, &tn.w2, &tn.tma, &tn.var[0], &tn.var[1],
+                           &tn.var[2], &ms, &tn.shfl, &tn.em);
     if (got < 13) continue;
-    if (got == 13) tn.shfl = 0;
+    if (got < 14) tn.shfl = 0;
+    if (got < 15) tn.em = 0;
     if (kk < 0 || kk > 1 || m < 0 || m > 31) continue;
     g_ctx.tuned[std::make_tuple(kk, hv, m)] = tn;  // m == 0: a batch tuning
     ++loaded;
