@@ -418,14 +418,16 @@ int darm_plan_describe(int dtype, size_t n, int has_vals, int variant, char* buf
  * tuning (nullable: the tuning a sort of this size would use): 7 int32 -
  * log2 tile, log2 elements per thread in tile/merge passes and in window
  * passes, log2 threads of a one-window pass, windows per window pass,
- * bulk-copy staging buffers, shuffle stages (0/1).  smem_limit: shared
+ * bulk-copy staging buffers, shuffle stages (bit 0 tile pass, bit 1 merge
+ * passes).  smem_limit: shared
  * memory per block the plan may use (0: the device's, or 227 KiB before
- * init).  Writes, per launch, 20 int32 - pass kind (0 tile, 1 window,
+ * init).  Writes, per launch, 21 int32 - pass kind (0 tile, 1 window,
  * 2 merge), compile-time tile/merge schedule, bulk-copy buffers, one-window
  * and two-window compile-time shapes, shuffle stages, log2 elements per
  * thread, form, grid, threads, shared memory bytes, then the block bit map
  * b, c, w0, s, log2 of the array length, rounds, persistent block count,
- * key map in and out - followed by 7 int32 per round: kind (0 registers
+ * key map in and out, two-round shuffle merge - followed by 7 int32 per
+ * round: kind (0 registers
  * only, 1 window), stage bit p, window bit a, layers, source and
  * destination (0 HBM, 1 shared memory), lane-divergent flag.  *count
  * receives the number of int32 needed; DARM_ERR_INVALID_ARG when cap is

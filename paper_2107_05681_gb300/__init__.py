@@ -548,7 +548,7 @@ def plan_describe(dtype: int, n: int, has_vals: bool, variant="melded") -> list[
 
 _LAUNCH_FIELDS = ("kind", "fixed", "tma", "win1", "win2", "shfl", "loge", "variant", "grid",
                   "threads", "smem", "b", "c", "w0", "s", "log2cap", "nrounds", "nblocks",
-                  "map_in", "map_out")
+                  "map_in", "map_out", "mshfl")
 _ROUND_FIELDS = ("kind", "p", "a", "cnt", "src", "dst", "lanediv")
 
 
@@ -571,8 +571,8 @@ def plan_dump(dtype: int, n: int, has_vals: bool, variant="melded", tuning=None,
                               ctypes.byref(cnt)), "darm_plan_dump")
     out, i = [], 0
     while i < buf.size:
-        L = dict(zip(_LAUNCH_FIELDS, (int(x) for x in buf[i:i + 20])))
-        i += 20
+        L = dict(zip(_LAUNCH_FIELDS, (int(x) for x in buf[i:i + 21])))
+        i += 21
         L["rounds"] = []
         for _ in range(L["nrounds"]):
             L["rounds"].append(dict(zip(_ROUND_FIELDS, (int(x) for x in buf[i:i + 7]))))

@@ -46,6 +46,7 @@ int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_
         L.win1 ? window1_kernel(kk == KEY_U64, has_vals, L.loge, int(L.P.c)).fn
         : L.win2 ? ((kk == KEY_U32) ? window2_kernel_u32(has_vals, L.loge, int(L.P.c), L.variant)
                                   : window2_kernel_u64(has_vals, L.loge, int(L.P.c), L.variant)).fn
+        : L.mshfl ? tma_merge_shfl_kernel_u32(L.loge, int(L.P.b), L.tma, L.variant, nullptr).fn
         : L.tma ? tma_merge_kernel_u32(has_vals, L.loge, int(L.P.b), L.tma, L.variant, nullptr).fn
         : L.shfl ? tile_shfl_kernel_u32(has_vals, L.loge, int(L.P.b), L.variant).fn
         : L.fixed ? fixed_kernel_fn(kk, has_vals, L.loge, int(L.P.b), L.variant, L.kind == PASS_MERGE)
@@ -161,6 +162,7 @@ int darm_sort_init(int device, size_t workspace_bytes) {
   for_each_tma_kernel_u32(set_smem_attr, st);
   for_each_tile_shfl_kernel_u32(set_smem_attr, st);
   for_each_pcm_kernel(set_smem_attr, st);
+  for_each_oddeven_kernel(set_smem_attr, st);
   for_each_window2_kernel(set_smem_attr, st);
   if (st[1] != 0) {
     fprintf(stderr, "darm: configuring shared memory failed: %s\n",
@@ -499,8 +501,8 @@ int darm_plan_dump(int dtype, size_t n, int has_vals, int variant, const int32_t
                             L.variant, int32_t(L.grid), int32_t(L.threads), int32_t(L.smem),
                             int32_t(L.P.b), int32_t(L.P.c), int32_t(L.P.w0), int32_t(L.P.s),
                             int32_t(L.P.log2cap), int32_t(L.P.nrounds), int32_t(L.P.nblocks),
-                            int32_t(L.P.map_in), int32_t(L.P.map_out)};
-    v.insert(v.end(), head, head + 20);
+                            int32_t(L.P.map_in), int32_t(L.P.map_out), L.mshfl};
+    v.insert(v.end(), head, head + 21);
     for (uint32_t r = 0; r < L.P.nrounds; ++r) {
       const Round& R = L.P.rounds[r];
       const int32_t row[] = {R.kind, R.p, R.a, R.cnt, R.src, R.dst, R.lanediv};

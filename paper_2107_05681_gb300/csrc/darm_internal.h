@@ -62,7 +62,9 @@ int segmented_parse(const uint64_t* seg_offsets, const uint32_t* seg_len, uint32
 cudaError_t launch_singletons(uint32_t* keys, uint32_t* vals, const uint64_t* base,
                               const uint32_t* len_desc, uint32_t n, cudaStream_t s);
 
-// PCM's merge-split kernels (pcm.cu), for the shared-memory limit set at init.
+// PCM's merge-split kernels (pcm.cu) and the odd-even bucket kernels
+// (oddeven.cu), for the shared-memory limit set at init.
 void for_each_pcm_kernel(void (*fn)(const void*, void*), void* ctx);
+void for_each_oddeven_kernel(void (*fn)(const void*, void*), void* ctx);
 
 }  // namespace darm

@@ -29,6 +29,9 @@ KernelEntry tile_shfl_kernel_u32(bool has_vals, int loge, int logt, int var);
 // (tma_merge.cuh); smem_bytes receives the dynamic shared memory they need.
 KernelEntry tma_merge_kernel_u32(bool has_vals, int loge, int logt, int ns, int var,
                                  size_t* smem_bytes);
+// The same merge in two rounds, its lower layers across lanes by shuffles
+// (keys only).
+KernelEntry tma_merge_shfl_kernel_u32(int loge, int logt, int ns, int var, size_t* smem_bytes);
 
 // Two-window passes with a compile-time shape (window2_kernel.cuh): E =
 // 2^loge, c low consecutive-element bits.

@@ -20,8 +20,9 @@
 //   - idle otherwise.
 // Every thread updates the elements it owns: the lower end keeps the
 // smaller key, the upper end the larger, both decided by the one predicate
-// key[upper] < key[lower], so equal keys never move.  Each layer reads into
-// registers, then (after a barrier) writes back.
+// key[upper] < key[lower], so equal keys never move.  The bucket lives in
+// two shared-memory buffers: each layer reads one and writes the other, so
+// one barrier separates layers.
 //
 // Divergent form: one branch per role, each with its own partner load and
 // compare.  Melded form (the paper's region-region meld, Algorithm 2): the
@@ -47,18 +48,25 @@ __global__ void __launch_bounds__(kOddEvenThreads, 1)
     darm_oddeven_block_kernel(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t n) {
   keys += size_t(blockIdx.x) * n;
   if (V) vals += size_t(blockIdx.x) * n;
-  __shared__ uint32_t sk[kOddEvenMax];
-  __shared__ uint32_t sv[V ? kOddEvenMax : 1];
+  // dynamic: two key buffers of n words, then (with a payload) two payload
+  // buffers
+  extern __shared__ __align__(16) uint32_t oe_smem[];
+  uint32_t* sk2[2] = {oe_smem, oe_smem + n};
+  uint32_t* sv2[2] = {oe_smem + 2 * n, oe_smem + 3 * n};
   const uint32_t tid = threadIdx.x;
   const uint32_t nt = blockDim.x;
   for (uint32_t x = tid; x < n; x += nt) {
-    sk[x] = keys[x];
-    if (V) sv[x] = vals[x];
+    sk2[0][x] = keys[x];
+    if (V) sv2[0][x] = vals[x];
   }
   __syncthreads();
+  uint32_t cur = 0;  // buffer holding the bucket before this layer
   for (uint32_t p = 1; p < n; p <<= 1) {
     for (uint32_t k = p; k >= 1; k >>= 1) {
-      uint32_t nk[kPerThread], nv[kPerThread];
+      const uint32_t* sk = cur ? sk2[1] : sk2[0];
+      const uint32_t* sv = cur ? sv2[1] : sv2[0];
+      uint32_t* dk = cur ? sk2[0] : sk2[1];
+      uint32_t* dv = cur ? sv2[0] : sv2[1];
 #pragma unroll
       for (int r = 0; r < kPerThread; ++r) {
         const uint32_t x = tid + uint32_t(r) * nt;
@@ -100,27 +108,28 @@ __global__ void __launch_bounds__(kOddEvenThreads, 1)
             }
           }
         }
-        nk[r] = key;
-        nv[r] = val;
+        dk[x] = key;
+        if (V) dv[x] = val;
       }
-      __syncthreads();
-#pragma unroll
-      for (int r = 0; r < kPerThread; ++r) {
-        const uint32_t x = tid + uint32_t(r) * nt;
-        if (x >= n) break;
-        sk[x] = nk[r];
-        if (V) sv[x] = nv[r];
-      }
+      cur ^= 1u;
       __syncthreads();
     }
   }
   for (uint32_t x = tid; x < n; x += nt) {
-    keys[x] = sk[x];
-    if (V) vals[x] = sv[x];
+    keys[x] = (cur ? sk2[1] : sk2[0])[x];
+    if (V) vals[x] = (cur ? sv2[1] : sv2[0])[x];
   }
 }
 
 }  // namespace
+
+void for_each_oddeven_kernel(void (*fn)(const void*, void*), void* ctx) {
+  fn(reinterpret_cast<const void*>(&darm_oddeven_block_kernel<false, 0>), ctx);
+  fn(reinterpret_cast<const void*>(&darm_oddeven_block_kernel<false, 1>), ctx);
+  fn(reinterpret_cast<const void*>(&darm_oddeven_block_kernel<true, 0>), ctx);
+  fn(reinterpret_cast<const void*>(&darm_oddeven_block_kernel<true, 1>), ctx);
+}
+
 }  // namespace darm
 
 using namespace darm;
@@ -139,16 +148,17 @@ extern "C" int darm_oddeven_sort_buckets(uint32_t* keys, uint32_t* vals, size_t 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool melded = variant != DARM_DIVERGENT;
   const uint32_t nb = uint32_t(bucket);
+  const size_t smem = size_t(vals ? 4 : 2) * nb * sizeof(uint32_t);
   if (vals) {
     if (melded)
-      darm_oddeven_block_kernel<true, 1><<<grid, threads, 0, s>>>(keys, vals, nb);
+      darm_oddeven_block_kernel<true, 1><<<grid, threads, smem, s>>>(keys, vals, nb);
     else
-      darm_oddeven_block_kernel<true, 0><<<grid, threads, 0, s>>>(keys, vals, nb);
+      darm_oddeven_block_kernel<true, 0><<<grid, threads, smem, s>>>(keys, vals, nb);
   } else {
     if (melded)
-      darm_oddeven_block_kernel<false, 1><<<grid, threads, 0, s>>>(keys, nullptr, nb);
+      darm_oddeven_block_kernel<false, 1><<<grid, threads, smem, s>>>(keys, nullptr, nb);
     else
-      darm_oddeven_block_kernel<false, 0><<<grid, threads, 0, s>>>(keys, nullptr, nb);
+      darm_oddeven_block_kernel<false, 0><<<grid, threads, smem, s>>>(keys, nullptr, nb);
   }
   if (cudaGetLastError() != cudaSuccess) return DARM_ERR_CUDA;
   g_ctx.launches.fetch_add(1, std::memory_order_relaxed);

@@ -244,7 +244,7 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
     Launch L{};
     L.kind = PASS_TILE;
     L.fixed = has_fixed(kk, has_vals, e1, t);
-    L.shfl = tn.shfl != 0 && has_shfl(kk, has_vals, e1, t);
+    L.shfl = (tn.shfl & 1) != 0 && has_shfl(kk, has_vals, e1, t);
     L.loge = e1;
     L.variant = pick_var(variant, tn, PASS_TILE);
     L.grid = uint32_t(1u << (m - t));
@@ -375,6 +375,30 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
         tma_smem <= smem_limit) {
       L.tma = tn.tma;
       L.smem = tma_smem;
+      if ((tn.shfl & 2) != 0 && !has_vals &&
+          tma_merge_shfl_kernel_u32(em, t, tn.tma, L.variant, nullptr).fn != nullptr) {
+        // two rounds: the top window from the staging buffer, then the lane
+        // layers by shuffles and the register layers
+        L.mshfl = true;
+        std::vector<Round> two;
+        Round r0{};
+        r0.kind = RK_WINDOW;
+        r0.p = uint8_t(p);
+        r0.a = uint8_t(t - em);
+        r0.cnt = uint8_t(em);
+        r0.src = LOC_GLOBAL;
+        r0.dst = LOC_SMEM;
+        Round r1{};
+        r1.kind = RK_WINDOW;
+        r1.p = uint8_t(p);
+        r1.a = 0;
+        r1.cnt = uint8_t(t - em);  // lane layers t-em-1 .. em, then em register layers
+        r1.src = LOC_SMEM;
+        r1.dst = LOC_GLOBAL;
+        two.push_back(r0);
+        two.push_back(r1);
+        set_rounds(L.P, two);
+      }
       L.P.nblocks = L.grid;
       int per_sm = 1;
       const void* tfn = tma_merge_kernel_u32(has_vals, em, t, tn.tma, L.variant, nullptr).fn;

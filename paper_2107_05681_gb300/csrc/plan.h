@@ -35,8 +35,10 @@ struct Tuning {
               // shared-memory exchange, 2*e2 layers per HBM sweep)
   int tma = 0; // merge passes of single arrays prefetch tiles with bulk copies
                // into this many staging buffers (0: plain merge kernel)
-  int shfl = 0; // tile passes of single arrays run stages 2E .. 32E across
-                // lanes with shuffles (tile_shfl_kernel.cuh) where built
+  int shfl = 0; // bit 0: tile passes of single arrays run stages 2E .. 32E
+                // across lanes with shuffles (tile_shfl_kernel.cuh); bit 1:
+                // bulk-copy merge passes run their lane layers by shuffles
+                // (two rounds instead of three), where built
   int em = 0;   // log2 elements per thread in merge passes (0: e1)
   int var[3]; // variant per pass kind (used when DARM_AUTO is requested)
 };
@@ -52,6 +54,7 @@ struct Launch {
   bool win2;   // two-window pass with a compile-time shape (window2_kernel.cuh)
   bool win1;   // one-window pass with a compile-time shape (window1_kernel.cuh)
   bool shfl;   // tile pass with shuffle stages (tile_shfl_kernel.cuh)
+  bool mshfl;  // bulk-copy merge in two rounds with shuffle layers
   int loge;
   int variant;
   uint32_t grid;

@@ -92,8 +92,28 @@ struct TmaMergeSmem {
 
 // Block size MAXT = threads of one tile; small tiles ask for 64 registers so
 // that several CTAs share an SM.
-template <typename K, bool V, int LOGE, int LOGT, int NS, int VAR, int MAXT>
+// SH (keys only): two rounds instead of three.  Round 0 runs the top LOGE
+// layers from the staging buffer into the work buffer as usual; round 1 loads
+// each thread's E consecutive keys, runs the layers whose partner is in
+// another lane of the warp with __shfl_xor_sync (partner strides E .. 16E)
+// and the layers below E in registers, and stores to HBM.  The direction is
+// uniform per tile, so no lane diverges.
+template <typename K, int LOGE, uint32_t MASK>
+__device__ __forceinline__ void merge_shfl_layer(K (&kr)[1 << LOGE], uint32_t lm, bool asc) {
+  const bool keep_min = ((threadIdx.x & lm) == 0u) == asc;
+#pragma unroll
+  for (int r = 0; r < (1 << LOGE); ++r) {
+    const K y = __shfl_xor_sync(MASK, kr[r], lm);
+    const K lo = kmin(kr[r], y);
+    const K hi = kmax(kr[r], y);
+    kr[r] = keep_min ? lo : hi;
+  }
+}
+
+template <typename K, bool V, int LOGE, int LOGT, int NS, int VAR, int MAXT, bool SH = false>
 __global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_kernel(const __grid_constant__ PassParams P) {
+  static_assert(!SH || (!V && MAXT >= 32 && LOGT - LOGE >= LOGE && LOGT - 2 * LOGE <= 5),
+                "two-round merge: keys only, the lane bits cover what the two windows leave");
   static_assert(NS >= 1 && NS <= 4, "one to four staging buffers");
   constexpr int E = 1 << LOGE;
   using L = TmaMergeSmem<K, V, LOGT, NS>;
@@ -167,6 +187,49 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_ke
     const bool asc = (((gblk | P.dir_base) & (1u << p) & capmask) == 0u);
     const uint32_t next = tile + uint32_t(NS) * gridDim.x;
 
+    if constexpr (SH) {
+      constexpr int A0 = LOGT - LOGE;  // round 0: window bits A0 .. LOGT-1
+      {
+        const uint32_t tl = (tid & ((1u << A0) - 1u)) | ((tid >> A0) << (A0 + LOGE));
+        auto body = [&](auto asc_c) {
+          constexpr bool ASC = decltype(asc_c)::value;
+#pragma unroll
+          for (int r = 0; r < E; ++r) kr[r] = stage_k[tl | (uint32_t(r) << A0)];
+          window_side<K, V, LOGE, ASC, true>(kr, vr, LOGE);
+          s_store<K, V, LOGE, A0, false, true>(kr, vr, false, gk, gv, 0u, sk, sv, phys(tl), 0u, K(0));
+        };
+        if (asc)
+          body(std::true_type{});
+        else
+          body(std::false_type{});
+      }
+      __syncthreads();
+      if (next < ntiles) {
+        if (tid == 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue(next, b);
+        }
+        pending |= 1u << b;
+      }
+      {
+        // round 1: E consecutive keys per thread; lane bits are index bits
+        // LOGE .. LOGE+4
+        const uint32_t tl = tid << LOGE;
+        s_load<K, V, LOGE, 0, false>(kr, vr, false, gk, gv, 0u, sk, sv, phys(tl), 0u, K(0));
+#pragma unroll
+        for (int q = A0 - 1; q >= LOGE; --q)
+          merge_shfl_layer<K, LOGE, 0xFFFFFFFFu>(kr, 1u << (q - LOGE), asc);
+        if (asc)
+          window_side<K, V, LOGE, true, true>(kr, vr, LOGE);
+        else
+          window_side<K, V, LOGE, false, true>(kr, vr, LOGE);
+        s_store<K, V, LOGE, 0, false, true>(kr, vr, true, gk, gv, tl | gblk, sk, sv, 0u, P.map_out,
+                                            K(0));
+      }
+      __syncthreads();
+      b = (b + 1 == NS) ? 0 : b + 1;
+      continue;
+    }
     static_for<0, NR>([&](auto I) {
       constexpr int IDX = decltype(I)::value;
       constexpr SRound R = SCHED::value.r[IDX];

@@ -6,15 +6,17 @@
 namespace darm {
 namespace {
 
-template <bool V, int LOGE, int LOGT, int NS>
+template <bool V, int LOGE, int LOGT, int NS, bool SH = false>
 KernelEntry mentry(int var, size_t* smem_bytes) {
   constexpr int MT = 1 << (LOGT - LOGE);
   if (smem_bytes) *smem_bytes = TmaMergeSmem<uint32_t, V, LOGT, NS>::kBytes;
   if (var)
-    return KernelEntry{
-        reinterpret_cast<const void*>(&darm_merge_tma_kernel<uint32_t, V, LOGE, LOGT, NS, 1, MT>), MT};
-  return KernelEntry{
-      reinterpret_cast<const void*>(&darm_merge_tma_kernel<uint32_t, V, LOGE, LOGT, NS, 0, MT>), MT};
+    return KernelEntry{reinterpret_cast<const void*>(
+                           &darm_merge_tma_kernel<uint32_t, V, LOGE, LOGT, NS, 1, MT, SH>),
+                       MT};
+  return KernelEntry{reinterpret_cast<const void*>(
+                         &darm_merge_tma_kernel<uint32_t, V, LOGE, LOGT, NS, 0, MT, SH>),
+                     MT};
 }
 
 template <bool V, int LOGE, int LOGT>
@@ -25,6 +27,12 @@ KernelEntry mpick(int ns, int var, size_t* smem_bytes) {
 }
 
 }  // namespace
+
+KernelEntry tma_merge_shfl_kernel_u32(int loge, int logt, int ns, int var, size_t* smem_bytes) {
+  if (loge == 5 && logt == 14 && ns == 2) return mentry<false, 5, 14, 2, true>(var, smem_bytes);
+  if (loge == 5 && logt == 13 && ns == 2) return mentry<false, 5, 13, 2, true>(var, smem_bytes);
+  return KernelEntry{nullptr, 0};
+}
 
 KernelEntry tma_merge_kernel_u32(bool has_vals, int loge, int logt, int ns, int var,
                                  size_t* smem_bytes) {
@@ -45,6 +53,10 @@ void for_each_tma_kernel_u32(void (*fn)(const void*, void*), void* ctx) {
       fn(tma_merge_kernel_u32(false, 5, 14, ns, var, nullptr).fn, ctx);
       fn(tma_merge_kernel_u32(false, 4, 14, ns, var, nullptr).fn, ctx);
     }
+  for (int var = 0; var < 2; ++var) {
+    fn(tma_merge_shfl_kernel_u32(5, 14, 2, var, nullptr).fn, ctx);
+    fn(tma_merge_shfl_kernel_u32(5, 13, 2, var, nullptr).fn, ctx);
+  }
 }
 
 }  // namespace darm

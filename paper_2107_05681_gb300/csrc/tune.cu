@@ -118,14 +118,15 @@ int darm_autotune(int dtype, size_t n, int has_vals, const char* db_path) {
               best = tn;
             }
           }
-  // the tile pass with shuffle stages instead of shared-memory rounds for
-  // strides E .. 16E, where one is built for the chosen shape
-  {
+  // shuffle stages: without them in the tile pass (0), and with the merge
+  // passes in two rounds as well (3), where built for the chosen shape
+  for (int shfl : {0, 3}) {
+    if (shfl == best.shfl) continue;
     Tuning tn = best;
-    tn.shfl = 1;
+    tn.shfl = shfl;
     std::vector<Launch> plan;
     float kind[3], tot;
-    if (plan_array(plan, kk, hv, m, tn, DARM_AUTO, 0, 0, g_ctx.smem_limit) && plan[0].shfl &&
+    if (plan_array(plan, kk, hv, m, tn, DARM_AUTO, 0, 0, g_ctx.smem_limit) &&
         time_plan(plan, kk, keys, vals, kbytes / 4, s, 3, kind, &tot) && tot < best_ms) {
       best_ms = tot;
       best = tn;

@@ -168,6 +168,10 @@ class Kernel:
     def round_layers(self, rd):
         """(stage p, register bits q of the layers, high to low)."""
         L, E = self.L, self.E
+        if self.kind == "tma_merge" and L.get("mshfl") and rd == 1:
+            # lane layers by shuffles, then the register layers: checked by
+            # _check_layers on the consecutive layout
+            return L["rounds"][0]["p"], []
         R = L["rounds"][rd] if self.kind not in ("window1",) else L["rounds"][0]
         if self.kind == "window2":
             R = L["rounds"][rd]
@@ -213,6 +217,20 @@ def check_launch_full(K, n, seq):
 def _check_layers(K, rd, g, seq):
     p, qs = K.round_layers(rd)
     R = K.L["rounds"][rd] if K.kind != "window1" else K.L["rounds"][0]
+    if K.kind == "tma_merge" and K.L.get("mshfl") and rd == 1:
+        # E consecutive elements per thread, lane b holding index bit E + b:
+        # the layers below the first window, lanes first, then registers
+        E = K.E
+        assert np.array_equal(g[..., 1:] - g[..., :-1], np.ones_like(g[..., 1:])), \
+            "two-round merge: registers are not consecutive"
+        top = R["a"] + R["cnt"]  # = the first window's lowest bit
+        lanes = 1 << (top - K.loge)
+        t = g[:, :lanes, 0]
+        assert np.all(t - t[:, :1] == np.arange(lanes)[None, :] * E), \
+            "two-round merge: lanes are not consecutive runs"
+        for q in range(top - 1, -1, -1):
+            seq.append((p, q))
+        return
     if R["kind"] == RK_PHASE_A and K.kind != "window2":
         # registers hold E consecutive elements (and lanes the next bits when
         # stages run across lanes): stages 1 .. p with every layer
@@ -300,6 +318,15 @@ def check_launch_linear(K, n, seq, rng):
         # layers: on single-bit images
         p, qs = K.round_layers(rd)
         R = L["rounds"][rd] if K.kind != "window1" else L["rounds"][0]
+        if K.kind == "tma_merge" and L.get("mshfl") and rd == 1:
+            off = nbits[0] + nbits[1]
+            top = R["a"] + R["cnt"]
+            assert images[off:off + K.loge] == [1 << i for i in range(K.loge)]
+            lane = images[nbits[0]:nbits[0] + (top - K.loge)]
+            assert lane == [1 << (K.loge + i) for i in range(top - K.loge)]
+            for q in range(top - 1, -1, -1):
+                seq.append((p, q))
+            continue
         if R["kind"] == RK_PHASE_A and K.kind != "window2":
             off = nbits[0] + nbits[1]
             assert images[off:off + K.loge] == [1 << i for i in range(K.loge)]

@@ -71,3 +71,30 @@ def test_float_keys(shfl_tuned, variant):
     ek, _ = oracle.bitonic_sort(keys, None)
     gk, _ = gpu_sort(darm, keys, None, variant=variant)
     assert_equal("keys", total_order_u32(gk), total_order_u32(ek))
+
+
+_MERGE2 = "0 0 {m} 14 5 5 8 2 2 1 1 1 0.0 3"
+
+
+@pytest.mark.parametrize("variant", ["divergent", "melded"])
+@pytest.mark.parametrize("desc", [False, True])
+def test_two_round_shuffle_merge(darm, tmp_path, variant, desc):
+    """The merge pass in two rounds (its lane layers by shuffles), selected by
+    bit 1 of the shuffle tuning field: the same network, bit for bit."""
+    db = str(tmp_path / "merge2.db")
+    with open(db, "w") as f:
+        for m in range(15, 22):
+            f.write(_MERGE2.format(m=m) + "\n")
+    darm.reset_tunings()
+    darm.load_tune_db(db)
+    try:
+        for m in (15, 18, 21):
+            n = 1 << m
+            lines = darm.plan_describe(darm.U32, n, False, variant)
+            assert any(ln.startswith("merge") and "rounds=2" in ln for ln in lines), lines
+            keys = synth.uniform_u32(980 + m, n) % np.uint32(n // 4)
+            ek, _ = oracle.bitonic_sort(keys, None, desc=desc)
+            gk, _ = gpu_sort(darm, keys, None, desc=desc, variant=variant)
+            assert_equal("keys", gk, ek)
+    finally:
+        darm.reset_tunings()

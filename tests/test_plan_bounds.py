@@ -18,7 +18,7 @@ KINDS = [(darm.U32, 4, False), (darm.U32, 4, True), (darm.F32, 4, False), (darm.
 
 @pytest.mark.parametrize("dtype,kb,hv", KINDS)
 def test_default_plans_every_size_enumerated(dtype, kb, hv):
-    for m in range(1, 19):
+    for m in range(1, 18):
         n = 1 << m
         for variant in ("melded", "divergent"):
             plan = darm.plan_dump(dtype, n, hv, variant)
@@ -42,7 +42,7 @@ def _tuner_candidates(hv):
             for e2 in (3, 4, 5):
                 for w2 in (1, 2):
                     for tma in (0, 1, 2):
-                        for shfl in (0, 1):
+                        for shfl in (0, 1, 3):
                             yield (t, e1, e2, 8, w2, tma, shfl)
 
 
@@ -73,10 +73,13 @@ def test_plans_of_each_kernel_kind_are_covered():
         for m in (12, 16, 18, 24, 26):
             for L in darm.plan_dump(dtype, 1 << m, hv, "melded"):
                 kinds.add(em.Kernel(L, kb, hv).kind)
-    for tn in ((14, 5, 5, 8, 1, 0, 0), (13, 5, 4, 8, 2, 0, 0)):
+    mshfl = False
+    for tn in ((14, 5, 5, 8, 1, 0, 0), (13, 5, 4, 8, 2, 0, 0), (14, 5, 5, 8, 2, 2, 3)):
         for L in darm.plan_dump(darm.U32, 1 << 18, False, "melded", tuning=tn):
             kinds.add(em.Kernel(L, 4, False).kind)
+            mshfl = mshfl or bool(L["mshfl"])
     assert {"tile_shfl", "tile_fixed", "tma_merge", "window1", "window2"} <= kinds, kinds
+    assert mshfl, "no plan with the two-round shuffle merge"
 
 
 @pytest.mark.parametrize("mutation", ["cnt", "a", "w0", "grid", "p"])
