@@ -927,7 +927,8 @@ def main():
                        "hbm_passes": passes, "tile": tile},
             "divergent": {"value": value_div, "ms_per_step": ms_div / args.steps},
             "melded_over_divergent": value / value_div,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "roofline": {"bound": "hbm" if passes > 1 else "latency",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": recorded_traffic(args.workload, dom),
                          "algorithmic_bytes": bytes_per_launch, "kernel": f"{dom} pass",
@@ -935,7 +936,9 @@ def main():
                          "whole_sort_gbs": whole_sort_gbs,
                          "whole_sort_frac": whole_sort_gbs / peak,
                          "pass_ms": {k: statistics.mean(v) for k, v in per_kind.items()},
-                         "pass_share": {k: totals[k] / sum(totals.values()) for k in totals}},
+                         "pass_share": {k: totals[k] / sum(totals.values()) for k in totals},
+                         **({"note": "one tile on one SM: every stage in one launch, bound "
+                                     "by latency, not by HBM"} if passes == 1 else {})},
             "clocks": clk,
             "gpu_launches": launches_meld + launches_div,
         }

@@ -7,7 +7,8 @@
 #include "batch.h"
 #include "darm.h"
 #include "darm_internal.h"
-#include "tile_kernel.cuh"
+#include "kernel_table.h"
+#include "tile_shfl_kernel.cuh"
 
 namespace darm {
 
@@ -72,13 +73,17 @@ int batch_append(BatchTables& bt, KeyKind kk, bool has_vals, const Tuning& tn, i
   auto pick = [&](PassKind k) { return (variant == DARM_AUTO) ? tn.var[k] : variant; };
 
   if (phase == 0) {
+    // the tile pass with shuffle stages, where one is built for this shape
+    const bool shfl = (tn.shfl & 1) != 0 && kk == KEY_U32 &&
+                      tile_shfl_seg_kernel_u32(has_vals, e, t, 1).fn != nullptr;
+    auto rounds_to = [&](int c) { return shfl ? shfl_rounds_through(c, t, e) : rounds_through(c, e); };
     std::vector<const BatchSeg*> order;
     for (const BatchSeg& s : segs)
       if (s.c >= e) order.push_back(&s);
     std::stable_sort(order.begin(), order.end(),
                      [](const BatchSeg* a, const BatchSeg* b) { return a->c > b->c; });
     // tile blocks, longest segments first
-    const int nr_full = rounds_through(t, e);
+    const int nr_full = rounds_to(t);
     size_t i = 0;
     while (i < order.size()) {
       const int c = order[i]->c;
@@ -108,7 +113,7 @@ int batch_append(BatchTables& bt, KeyKind kk, bool has_vals, const Tuning& tn, i
         SegBlock B{};
         B.first_slot = first;
         B.log2cap = uint8_t(c);
-        B.nrounds = uint8_t(rounds_through(c, e));
+        B.nrounds = uint8_t(rounds_to(c));
         B.final_pass = 1;
         B.fill = 1;
         bt.blocks.push_back(B);
@@ -125,11 +130,13 @@ int batch_append(BatchTables& bt, KeyKind kk, bool has_vals, const Tuning& tn, i
       L.P.b = L.P.c = L.P.w0 = uint32_t(t);
       L.P.log2cap = uint32_t(t);
       L.P.map_in = map_in;
-      const std::vector<Round> rs = tile_rounds(t, e);
+      const std::vector<Round> rs = shfl ? tile_rounds_shfl(t, e) : tile_rounds(t, e);
       L.P.nrounds = uint32_t(rs.size());
       for (size_t r = 0; r < rs.size(); ++r) L.P.rounds[r] = rs[r];
-      const void* fn = fixed_kernel_fn(kk, has_vals, e, t, L.variant, false);
+      const void* fn = shfl ? tile_shfl_seg_kernel_u32(has_vals, e, t, L.variant).fn
+                            : fixed_kernel_fn(kk, has_vals, e, t, L.variant, false);
       L.fixed = fn != nullptr;
+      L.shfl = shfl;
       if (L.fixed) {
         L.P.nblocks = tile_blocks;
         L.grid = uint32_t(std::min<int>(int(tile_blocks), occupancy_grid(fn, int(L.threads), L.smem)));

@@ -48,7 +48,8 @@ int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_
                                   : window2_kernel_u64(has_vals, L.loge, int(L.P.c), L.variant)).fn
         : L.mshfl ? tma_merge_shfl_kernel_u32(L.loge, int(L.P.b), L.tma, L.variant, nullptr).fn
         : L.tma ? tma_merge_kernel_u32(has_vals, L.loge, int(L.P.b), L.tma, L.variant, nullptr).fn
-        : L.shfl ? tile_shfl_kernel_u32(has_vals, L.loge, int(L.P.b), L.variant).fn
+        : L.shfl ? (L.P.blocks ? tile_shfl_seg_kernel_u32(has_vals, L.loge, int(L.P.b), L.variant)
+                               : tile_shfl_kernel_u32(has_vals, L.loge, int(L.P.b), L.variant)).fn
         : L.fixed ? fixed_kernel_fn(kk, has_vals, L.loge, int(L.P.b), L.variant, L.kind == PASS_MERGE)
                   : kernel_fn(kk, has_vals, L.loge, L.variant);
     if (!fn) return DARM_ERR_INVALID_ARG;

@@ -24,6 +24,8 @@ KernelEntry tile_kernel_u64(bool has_vals, int loge, int logt, int var, bool mer
 // Tile passes whose stages 2E .. 32E run across lanes with shuffles
 // (tile_shfl_kernel.cuh), whole arrays only; {nullptr, 0} when not built.
 KernelEntry tile_shfl_kernel_u32(bool has_vals, int loge, int logt, int var);
+// The same pass for batched segments (block tables, persistent launch).
+KernelEntry tile_shfl_seg_kernel_u32(bool has_vals, int loge, int logt, int var);
 
 // Persistent merge kernels that prefetch tiles with bulk copies
 // (tma_merge.cuh); smem_bytes receives the dynamic shared memory they need.

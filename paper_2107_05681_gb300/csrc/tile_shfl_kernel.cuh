@@ -25,7 +25,8 @@
 // thread's keys for the stage (~x reverses unsigned order) and runs the
 // ascending copy only.
 //
-// Whole arrays only (no segment tables): a launch has one CTA per tile.
+// Whole arrays (one CTA per tile) and batched segments (a persistent launch
+// over a block table, as the plain tile pass).
 #pragma once
 
 #include "tile_kernel.cuh"
@@ -123,47 +124,108 @@ __device__ __forceinline__ void shfl_layer(K (&kr)[1 << LOGE], uint32_t (&vr)[1 
   }
 }
 
-template <typename K, bool V, int LOGE, int LOGT, int VAR, int MAXT>
-__global__ void __launch_bounds__(MAXT, tile_min_blocks(MAXT))
-    darm_tile_shfl_kernel(const __grid_constant__ PassParams P) {
+// Rounds of the schedule through stage 2^c (a segment of capacity 2^c stops
+// there): the first round holds every stage up to 2^(LOGE+S).
+__host__ __device__ constexpr int shfl_rounds_through(int c, int t, int e) {
+  int n = 1;
+  for (int p = e + shfl_stages(t, e) + 1; p <= c; ++p) n += (p + e - 1) / e;
+  return n;
+}
+
+// One tile of the pass.  `bidx` is the block number, or the entry of the
+// segmented block table (segments padded with sentinels, small segments
+// packed into one tile, as in tile_kernel.cuh's tile_block).
+template <typename K, bool V, int LOGE, int LOGT, int VAR, uint32_t MASK, bool SEG>
+__device__ __forceinline__ void tile_block_shfl(const PassParams& P, uint32_t bidx, K* sk,
+                                                uint32_t* sv) {
   constexpr int E = 1 << LOGE;
   constexpr int S = shfl_stages(LOGT, LOGE);
-  constexpr int LANES = (MAXT < 32) ? MAXT : 32;
-  constexpr uint32_t MASK = (LANES == 32) ? 0xFFFFFFFFu : ((1u << LANES) - 1u);
-  static_assert(MAXT == (1 << (LOGT - LOGE)), "one tile per CTA");
-  static_assert((1 << S) <= LANES, "shuffle stages stay inside a warp");
   constexpr int PADT = TilePad<K, V, LOGE>::value;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  K* sk = reinterpret_cast<K*>(smem_raw);
-  uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + sizeof(K) * smem_words(1u << LOGT));
   K* __restrict__ gk = reinterpret_cast<K*>(P.keys);
   uint32_t* __restrict__ gv = P.vals;
   const uint32_t tid = threadIdx.x;
-  const uint32_t gblk = blockIdx.x << LOGT;
-  const uint32_t capmask = (1u << P.log2cap) - 1u;
+
+  uint32_t blk = bidx;
+  uint32_t log2cap = P.log2cap;
+  uint32_t nrounds = P.nrounds;
+  bool final_pass = true;
+  bool fill = false;
+  const SegSlot* slots = nullptr;
+  if (SEG && P.blocks != nullptr) {
+    const SegBlock B = P.blocks[bidx];
+    blk = B.blk_in_seg;
+    log2cap = B.log2cap;
+    nrounds = B.nrounds;
+    final_pass = B.final_pass != 0;
+    fill = B.fill != 0;
+    slots = P.slots + B.first_slot;
+  }
+  const uint32_t gblk = blk << LOGT;
+  const uint32_t capmask = (1u << log2cap) - 1u;
 
   K kr[E];
   uint32_t vr[E];
 #pragma unroll
-  for (int r = 0; r < E; ++r) vr[r] = 0;
+  for (int r = 0; r < E; ++r) {
+    if (SEG) kr[r] = K(0);  // threads of an unused slot shuffle these
+    vr[r] = 0;
+  }
 
   using SCHED = ShflSchedule<LOGT, LOGE>;
   constexpr int NR = SCHED::count;
-
+  bool done = false;
   static_for<0, NR>([&](auto I) {
     constexpr int IDX = decltype(I)::value;
     constexpr SRound R = SCHED::value.r[IDX];
     constexpr int A = R.a;
-    const bool to_global = (R.dst == LOC_GLOBAL);
+    if (SEG && done) return;
+    // whole arrays run every round: `last` is a compile-time constant there
+    const bool last = SEG ? (uint32_t(IDX) + 1 == nrounds) : (IDX + 1 == NR);
+    const bool from_global = (R.src == LOC_GLOBAL);
+    const bool to_global = last || (R.dst == LOC_GLOBAL);
     const uint32_t tl = (tid & ((1u << A) - 1u)) | ((tid >> A) << (A + LOGE));
     const uint32_t g_full = tl | gblk;
     const uint32_t s_base = Interleave<K, V>::value ? phys8(tl) : physp<PADT>(tl);
+    uint32_t min_ = 0, mout = 0, g_t = g_full;
+    K* bk = gk;
+    uint32_t* bv = gv;
+    uint32_t seg_len = 0xFFFFFFFFu;
+    bool skip = false;  // unused slot of a packed block: touch no memory
+    if (SEG && slots != nullptr && (from_global || to_global)) {
+      const SegSlot Sl = slots[g_full >> log2cap];
+      bk = gk + Sl.base;
+      if (V) bv = gv + Sl.base;
+      seg_len = Sl.len;
+      skip = (Sl.flags & kSlotEmpty) != 0;
+      const uint32_t f = P.map_in | ((Sl.flags & kSlotDesc) ? kMapComplement : 0u);
+      if (IDX == 0 && from_global && fill) min_ = f;
+      if (last && final_pass) mout = f;
+      g_t = g_full & capmask;
+    } else {
+      if (IDX == 0 && from_global) min_ = P.map_in;
+      if (last) mout = P.map_out;
+    }
     const uint32_t g_dir = (g_full | P.dir_base) & capmask;
-    const uint32_t mout = to_global ? P.map_out : 0u;
+    const bool do_store = !(to_global && skip);
     if constexpr (R.kind == RK_PHASE_A) {
-      s_load<K, V, LOGE, 0, false, PADT>(kr, vr, true, gk, gv, g_full, sk, sv, s_base, P.map_in, K(0));
-      phase_a_small<K, V, LOGE>(kr, vr, P.log2cap);
-      if (uint32_t(LOGE) <= P.log2cap) {
+      if (!skip)
+        s_load<K, V, LOGE, 0, false, PADT>(kr, vr, true, bk, bv, g_t, sk, sv, s_base, min_, K(0));
+      if (SEG && fill) {
+        bool collide = false;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const uint32_t pos = g_t + uint32_t(r);
+          if (pos >= seg_len) {
+            kr[r] = ~K(0);
+            if (V) vr[r] = 0xFFFFFFFFu;
+          } else if (V && kr[r] == ~K(0)) {
+            collide = true;
+          }
+        }
+        if (collide && !skip && P.status != nullptr) atomicOr(P.status, int(kStatusSentinelCollision));
+      }
+      phase_a_small<K, V, LOGE>(kr, vr, log2cap);
+      if (uint32_t(LOGE) <= log2cap) {
         const bool asc = ((g_dir & uint32_t(E)) == 0u);
         if (VAR == kDivergent) {
           if (asc)
@@ -179,11 +241,13 @@ __global__ void __launch_bounds__(MAXT, tile_min_blocks(MAXT))
           for (int r = 0; r < E; ++r) kr[r] ^= m;
         }
       }
-      // stages 2E .. 2^(LOGE+S): lane layers by shuffles, then registers
+      // stages 2E .. 2^(LOGE+S): lane layers by shuffles, then registers.
+      // The condition is uniform per block (one capacity per block), so
+      // every lane of a warp takes part in every shuffle.
       static_for<1, S + 1>([&](auto SI) {
         constexpr int P_ = LOGE + decltype(SI)::value;
-        if (uint32_t(P_) > P.log2cap) return;
-        const bool asc = ((g_dir & (1u << P_)) == 0u) || uint32_t(P_) == P.log2cap;
+        if (uint32_t(P_) > log2cap) return;
+        const bool asc = ((g_dir & (1u << P_)) == 0u);
         constexpr bool LANEDIV = (P_ - LOGE) < 5;  // bit P_ is a lane bit
         const K m = (VAR == kMelded && LANEDIV && !asc) ? ~K(0) : K(0);
         if (VAR == kMelded && LANEDIV) {
@@ -205,32 +269,72 @@ __global__ void __launch_bounds__(MAXT, tile_min_blocks(MAXT))
           for (int r = 0; r < E; ++r) kr[r] ^= m;
         }
       });
-      s_store<K, V, LOGE, 0, false, false, PADT>(kr, vr, to_global, gk, gv, g_full, sk, sv, s_base,
-                                                 mout, K(0));
+      if (do_store)
+        s_store<K, V, LOGE, 0, false, false, PADT>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base,
+                                                   mout, K(0));
     } else {
       const bool asc = ((g_dir & (1u << R.p)) == 0u);
       if (VAR == kDivergent || !R.lanediv) {
         if (asc) {
-          s_load<K, V, LOGE, A, false, PADT>(kr, vr, false, gk, gv, g_full, sk, sv, s_base, 0u, K(0));
+          s_load<K, V, LOGE, A, false, PADT>(kr, vr, false, bk, bv, g_t, sk, sv, s_base, 0u, K(0));
           window_side<K, V, LOGE, true>(kr, vr, R.cnt);
-          s_store<K, V, LOGE, A, false, false, PADT>(kr, vr, to_global, gk, gv, g_full, sk, sv, s_base,
-                                                     mout, K(0));
+          if (do_store)
+            s_store<K, V, LOGE, A, false, false, PADT>(kr, vr, to_global, bk, bv, g_t, sk, sv,
+                                                       s_base, mout, K(0));
         } else {
-          s_load<K, V, LOGE, A, true, PADT>(kr, vr, false, gk, gv, g_full, sk, sv, s_base, 0u, K(0));
+          s_load<K, V, LOGE, A, true, PADT>(kr, vr, false, bk, bv, g_t, sk, sv, s_base, 0u, K(0));
           window_side<K, V, LOGE, false>(kr, vr, R.cnt);
-          s_store<K, V, LOGE, A, true, false, PADT>(kr, vr, to_global, gk, gv, g_full, sk, sv, s_base,
-                                                    mout, K(0));
+          if (do_store)
+            s_store<K, V, LOGE, A, true, false, PADT>(kr, vr, to_global, bk, bv, g_t, sk, sv,
+                                                      s_base, mout, K(0));
         }
       } else {
         const K m = asc ? K(0) : ~K(0);
-        s_load<K, V, LOGE, A, false, PADT>(kr, vr, false, gk, gv, g_full, sk, sv, s_base, 0u, m);
+        s_load<K, V, LOGE, A, false, PADT>(kr, vr, false, bk, bv, g_t, sk, sv, s_base, 0u, m);
         window_side<K, V, LOGE, true>(kr, vr, R.cnt);
-        s_store<K, V, LOGE, A, false, false, PADT>(kr, vr, to_global, gk, gv, g_full, sk, sv, s_base,
-                                                   mout, m);
+        if (do_store)
+          s_store<K, V, LOGE, A, false, false, PADT>(kr, vr, to_global, bk, bv, g_t, sk, sv, s_base,
+                                                     mout, m);
       }
     }
-    if (!to_global) __syncthreads();
+    if (to_global) {
+      done = true;
+    } else {
+      __syncthreads();
+    }
   });
+  (void)done;
+}
+
+// SEG: the launch may address segments through a block table and take
+// blocks persistently (batched sorts); without it, whole arrays only (the
+// table logic compiled out, which spares registers).
+template <typename K, bool V, int LOGE, int LOGT, int VAR, int MAXT, bool SEG = false>
+__global__ void __launch_bounds__(MAXT, tile_min_blocks(MAXT))
+    darm_tile_shfl_kernel(const __grid_constant__ PassParams P) {
+  constexpr int S = shfl_stages(LOGT, LOGE);
+  constexpr int LANES = (MAXT < 32) ? MAXT : 32;
+  constexpr uint32_t MASK = (LANES == 32) ? 0xFFFFFFFFu : ((1u << LANES) - 1u);
+  static_assert(MAXT == (1 << (LOGT - LOGE)), "one tile per CTA");
+  static_assert((1 << S) <= LANES, "shuffle stages stay inside a warp");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  K* sk = reinterpret_cast<K*>(smem_raw);
+  uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + sizeof(K) * smem_words(1u << LOGT));
+  if (!SEG || P.work_counter == nullptr) {
+    tile_block_shfl<K, V, LOGE, LOGT, VAR, MASK, SEG>(P, blockIdx.x, sk, sv);
+    return;
+  }
+  // persistent: blocks of the table (longest segments first) are taken in
+  // order from a global counter as CTAs become free
+  __shared__ uint32_t s_next;
+  for (;;) {
+    if (threadIdx.x == 0) s_next = atomicAdd(P.work_counter, 1u);
+    __syncthreads();
+    const uint32_t b = s_next;
+    __syncthreads();
+    if (b >= P.nblocks) break;
+    tile_block_shfl<K, V, LOGE, LOGT, VAR, MASK, SEG>(P, b, sk, sv);
+  }
 }
 
 }  // namespace darm

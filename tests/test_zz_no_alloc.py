@@ -10,6 +10,7 @@ so that a run stopping at the first failure has run every other test first;
 it also passes alone in a fresh process.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -77,6 +78,7 @@ def test_noalloc_allocates_no_device_memory(darm):
     k, v = src_k.clone(), src_v.clone()
     _call_noalloc(darm, k, v, segs, "melded", None)  # first call: one-time set-up
     torch.cuda.synchronize()
+    gc.collect()  # tensors of earlier tests freed now, not during the loop
     free0 = torch.cuda.mem_get_info()[0]
     alloc0 = torch.cuda.memory_allocated()
     for _ in range(3):
@@ -87,7 +89,9 @@ def test_noalloc_allocates_no_device_memory(darm):
         _call_noalloc(darm, k, v, segs, "melded", None)
         torch.cuda.synchronize()
         assert torch.cuda.mem_get_info()[0] == before
-    assert torch.cuda.memory_allocated() == alloc0
+    # torch's allocator served no new block (a late collection of an earlier
+    # test's tensor may only lower the count)
+    assert torch.cuda.memory_allocated() <= alloc0
     assert torch.cuda.mem_get_info()[0] == free0
 
 
