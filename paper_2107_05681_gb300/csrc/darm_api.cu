@@ -1,6 +1,8 @@
 // darm_api.cu - the C ABI (include/darm.h): context, whole-array sorts,
 // host-buffer sorts, plan introspection and the launch path shared by the
 // segmented sort and the serving loop.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,6 +36,21 @@ const void* fixed_kernel_fn(KeyKind kk, bool has_vals, int loge, int logt, int v
   return e.fn;
 }
 
+// Tensor map of `rows` rows of 32 uint32 keys (128 bytes) from `keys`,
+// read and written in boxes of `box_rows` rows with the 128-byte swizzle
+// (the swizzled in-place merge pass).
+static bool encode_key_rows(CUtensorMap* tm, void* keys, uint64_t rows, uint32_t box_rows) {
+  if (g_encode_tiled == nullptr) return false;
+  auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(g_encode_tiled);
+  const cuuint64_t dims[2] = {32, rows};
+  const cuuint64_t strides[1] = {128};
+  const cuuint32_t box[2] = {32, box_rows};
+  const cuuint32_t elem_strides[2] = {1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, keys, dims, strides, box, elem_strides,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_t* vals,
                 cudaStream_t stream, bool count) {
   const bool has_vals = vals != nullptr;
@@ -53,7 +70,17 @@ int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_
         : L.fixed ? fixed_kernel_fn(kk, has_vals, L.loge, int(L.P.b), L.variant, L.kind == PASS_MERGE)
                   : kernel_fn(kk, has_vals, L.loge, L.variant);
     if (!fn) return DARM_ERR_INVALID_ARG;
-    void* args[] = {&P};
+    CUtensorMap tmap;
+    void* args[] = {&P, &tmap};
+    if (L.tma == 3) {
+      // the tiles this launch covers, as rows of 32 keys from `keys`
+      const int rows_log2 = int(L.P.b) - 5;
+      const uint64_t rows = uint64_t(L.P.nblocks) << rows_log2;
+      if (!encode_key_rows(&tmap, keys, rows, rows_log2 >= 8 ? 256u : (1u << rows_log2))) {
+        fprintf(stderr, "darm: encoding the merge pass's tensor map failed\n");
+        return DARM_ERR_CUDA;
+      }
+    }
     cudaError_t err = cudaLaunchKernel(fn, dim3(L.grid), dim3(L.threads), args, L.smem, stream);
     if (err != cudaSuccess) {
       fprintf(stderr, "darm: launch failed: %s\n", cudaGetErrorString(err));
@@ -154,6 +181,17 @@ int darm_sort_init(int device, size_t workspace_bytes) {
   g_ctx.device = device;
   g_ctx.sms = sms;
   g_sms_for_plans = sms;
+  {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    cudaGetLastError();
+    g_encode_tiled = fn;
+    g_tensor_maps = fn != nullptr ? 1 : 0;
+  }
   g_ctx.smem_limit = size_t(optin);
   int st[2] = {optin, 0};
   for_each_kernel_u32(set_smem_attr, st);

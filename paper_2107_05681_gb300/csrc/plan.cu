@@ -51,6 +51,8 @@ static bool has_shfl(KeyKind kk, bool has_vals, int loge, int logt) {
 }
 
 int g_sms_for_plans = 152;
+void* g_encode_tiled = nullptr;
+int g_tensor_maps = -1;
 
 static int max_threads(KeyKind kk, bool has_vals, int loge) {
   KernelEntry e = (kk == KEY_U32) ? kernel_u32(has_vals, loge, 1) : kernel_u64(has_vals, loge, 1);
@@ -66,7 +68,9 @@ Tuning default_tuning(KeyKind kk, bool has_vals) {
     tn.e2 = 5;  // window passes: 10 layers per HBM sweep
     tn.c2 = 8;
     tn.w2 = 2;
-    tn.tma = 2;  // two tiles stream in while one is merged (200 KiB per SM)
+    tn.tma = 3;  // in place, three swizzled tiles, bulk tensor stores: 2^26
+                 // float keys, merge pass 117 -> 96 us (else 2: two dense
+                 // staging buffers)
     tn.shfl = 1;  // 2^26 float keys: tile pass 0.686 -> 0.639 ms
   } else if (words == 2) {
     tn.t = 12;  // 4 Ki (key, payload) pairs = 36 KiB with padding: four CTAs per SM
@@ -370,13 +374,18 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
     // single arrays: the persistent merge that streams the next tile in with
     // bulk copies while the current one is processed (one CTA per SM)
     size_t tma_smem = 0;
-    if (kk == KEY_U32 && tn.tma &&
-        tma_merge_kernel_u32(has_vals, em, t, tn.tma, L.variant, &tma_smem).fn != nullptr &&
+    int tma = tn.tma;
+    if (tma == 3 && (g_tensor_maps == 0 ||
+                     tma_merge_kernel_u32(has_vals, em, t, 3, L.variant, &tma_smem).fn == nullptr ||
+                     tma_smem > smem_limit))
+      tma = 2;  // no swizzled kernel for this shape (or no tensor maps)
+    if (kk == KEY_U32 && tma &&
+        tma_merge_kernel_u32(has_vals, em, t, tma, L.variant, &tma_smem).fn != nullptr &&
         tma_smem <= smem_limit) {
-      L.tma = tn.tma;
+      L.tma = tma;
       L.smem = tma_smem;
       if ((tn.shfl & 2) != 0 && !has_vals &&
-          tma_merge_shfl_kernel_u32(em, t, tn.tma, L.variant, nullptr).fn != nullptr) {
+          tma_merge_shfl_kernel_u32(em, t, tma, L.variant, nullptr).fn != nullptr) {
         // two rounds: the top window from the staging buffer, then the lane
         // layers by shuffles and the register layers
         L.mshfl = true;
@@ -401,7 +410,7 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
       }
       L.P.nblocks = L.grid;
       int per_sm = 1;
-      const void* tfn = tma_merge_kernel_u32(has_vals, em, t, tn.tma, L.variant, nullptr).fn;
+      const void* tfn = tma_merge_kernel_u32(has_vals, em, t, tma, L.variant, nullptr).fn;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tfn, int(L.threads), L.smem) !=
               cudaSuccess ||
           per_sm < 1) {

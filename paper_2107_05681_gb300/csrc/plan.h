@@ -46,11 +46,20 @@ struct Tuning {
 // SM count the planner sizes persistent launches for (set at init).
 extern int g_sms_for_plans;
 
+// The driver's tensor-map encoder (cuTensorMapEncodeTiled), looked up at
+// init.  g_tensor_maps: 1 found, 0 missing (no merge pass then uses the
+// swizzled in-place kernel, tma == 3), -1 before init (plans made for
+// inspection assume a driver that has it, as every CUDA 12+ driver does).
+extern void* g_encode_tiled;
+extern int g_tensor_maps;
+
 struct Launch {
   PassKind kind;
   bool fixed;  // compile-time-schedule tile/merge kernel (tile_kernel.cuh)
   int tma;     // persistent merge with bulk-copy prefetch into this many
-               // staging buffers (tma_merge.cuh); 0: plain merge kernel
+               // staging buffers (tma_merge.cuh); 3: in place in three
+               // swizzled tile buffers with bulk tensor stores
+               // (tma_merge_swz.cuh); 0: plain merge kernel
   bool win2;   // two-window pass with a compile-time shape (window2_kernel.cuh)
   bool win1;   // one-window pass with a compile-time shape (window1_kernel.cuh)
   bool shfl;   // tile pass with shuffle stages (tile_shfl_kernel.cuh)

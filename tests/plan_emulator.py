@@ -43,6 +43,41 @@ def physp(l, pad):
     return l + (l >> 5) * pad
 
 
+def swz128(l):
+    """Word of element l in a tile buffer written by a TMA copy with the
+    128-byte swizzle: 16-byte chunk c of 128-byte row w holds chunk c ^ (w & 7)."""
+    return l ^ (((l >> 5) & 7) << 2)
+
+
+def swz_kernel_word(tid, r, rd, logt):
+    """The word offsets the swizzled in-place merge kernel computes
+    (tma_merge_swz.cuh) for register r of thread tid in round rd."""
+    if rd == 0:
+        return (tid ^ (((tid >> 5) & 7) << 2)) + (r << (logt - 5))
+    if rd == 1:
+        return ((tid >> 5) << 10) + (r << 5) + ((tid & 31) ^ ((r & 7) << 2))
+    return (tid << 5) + ((((r >> 2) ^ (tid & 7)) << 2) | (r & 3))
+
+
+def check_swz_merge(K):
+    """The swizzled merge runs a fixed schedule: it must be the plan's, and
+    the kernel's own word offsets must be the swizzled slot of the element
+    the register holds, in every round (the rounds work in place)."""
+    L = K.L
+    b = L["b"]
+    assert K.loge == 5 and b in (13, 14) and not K.hv and K.kb == 4, "swizzled merge shape"
+    assert L["threads"] == 1 << (b - 5)
+    got = [(R["a"], R["cnt"]) for R in L["rounds"]]
+    assert got == [(b - 5, b - 10), (5, 5), (0, 5)], ("swizzled merge rounds", got)
+    tid = np.arange(L["threads"], dtype=np.int64)[:, None]
+    r = np.arange(32, dtype=np.int64)[None, :]
+    for rd in range(3):
+        l = K.local(tid, r, K.window_of(rd))
+        w = swz_kernel_word(tid, r, rd, b)
+        assert np.array_equal(w, swz128(l)), ("swizzled merge word offsets", rd)
+        assert w.min() >= 0 and w.max() < (1 << b) and np.unique(w).size == w.size
+
+
 def smem_words(elems):
     return elems + ((elems >> 5) << 2) + 4
 
@@ -61,6 +96,8 @@ class Kernel:
             self.kind = "window1"
         elif L["win2"]:
             self.kind = "window2"
+        elif L["tma"] == 3:
+            self.kind = "swz_merge"
         elif L["tma"]:
             self.kind = "tma_merge"
         elif L["shfl"]:
@@ -78,6 +115,8 @@ class Kernel:
         return 4
 
     def slot(self, l):
+        if self.kind == "swz_merge":
+            return swz128(l)
         if self.interleave:
             return phys8(l)
         if self.kind in ("tile_fixed", "tile_shfl", "window2"):
@@ -86,6 +125,8 @@ class Kernel:
 
     def slot_bound(self):
         b = self.L["b"]
+        if self.kind == "swz_merge":
+            return 1 << b
         if self.kind == "window2":
             b = self.L["c"] + 2 * self.loge
         return smem_words(1 << b)
@@ -98,7 +139,7 @@ class Kernel:
 
     def gblk(self, blk):
         L = self.L
-        if self.kind in ("tile_fixed", "tile_shfl", "tma_merge"):
+        if self.kind in ("tile_fixed", "tile_shfl", "tma_merge", "swz_merge"):
             return blk << L["b"]
         c, w0 = L["c"], L["w0"]
         nmid = w0 - c
@@ -108,7 +149,7 @@ class Kernel:
 
     def gmap(self, l):
         L = self.L
-        if self.kind in ("tile_fixed", "tile_shfl", "tma_merge"):
+        if self.kind in ("tile_fixed", "tile_shfl", "tma_merge", "swz_merge"):
             return l
         c, w0 = L["c"], L["w0"]
         return (l & ((1 << c) - 1)) | ((l >> c) << w0)
@@ -175,7 +216,7 @@ class Kernel:
         R = L["rounds"][rd] if self.kind not in ("window1",) else L["rounds"][0]
         if self.kind == "window2":
             R = L["rounds"][rd]
-        if self.kind in ("tma_merge",) or (self.kind == "tile_fixed" and L["kind"] == MERGE):
+        if self.kind in ("tma_merge", "swz_merge") or (self.kind == "tile_fixed" and L["kind"] == MERGE):
             p = L["rounds"][0]["p"]
         else:
             p = R["p"]
@@ -185,7 +226,7 @@ class Kernel:
 
 def _grid_arrays(K):
     L = K.L
-    blocks = L["nblocks"] if K.kind == "tma_merge" else L["grid"]
+    blocks = L["nblocks"] if K.kind in ("tma_merge", "swz_merge") else L["grid"]
     blk = np.arange(blocks, dtype=np.int64)[:, None, None]
     tid = np.arange(L["threads"], dtype=np.int64)[None, :, None]
     r = np.arange(K.E, dtype=np.int64)[None, None, :]
@@ -195,6 +236,8 @@ def _grid_arrays(K):
 def check_launch_full(K, n, seq):
     """Enumerate every (block, thread, register) of every round."""
     blk, tid, r = _grid_arrays(K)
+    if K.kind == "swz_merge":
+        check_swz_merge(K)
     for rd in range(K.nrounds()):
         a = K.window_of(rd)
         l = K.local(tid, r, a) + 0 * blk
@@ -205,7 +248,7 @@ def check_launch_full(K, n, seq):
         if K.touches_hbm(rd):
             h = K.hbm_address(blk, tid, r, rd) + 0 * g
             assert np.array_equal(h, g), (K.kind, rd, "HBM address differs from the element")
-        if K.kind in ("tile_fixed", "tile_shfl", "tma_merge", "window2", "generic") and (
+        if K.kind in ("tile_fixed", "tile_shfl", "tma_merge", "swz_merge", "window2", "generic") and (
                 K.kind != "generic" or K.L["smem"] > 0) and K.kind != "window1":
             s = K.slot(l)
             assert s.min() >= 0 and s.max() < K.slot_bound(), (K.kind, rd, "slot out of range")
@@ -278,7 +321,9 @@ def check_launch_linear(K, n, seq, rng):
     """Large arrays: the maps are ORs of shifted bit fields; check them on
     single bits and random samples instead of enumerating."""
     L = K.L
-    blocks = L["nblocks"] if K.kind == "tma_merge" else L["grid"]
+    blocks = L["nblocks"] if K.kind in ("tma_merge", "swz_merge") else L["grid"]
+    if K.kind == "swz_merge":
+        check_swz_merge(K)
     nbits = [blocks.bit_length() - 1, L["threads"].bit_length() - 1, K.loge]
     assert (1 << nbits[0]) == blocks and (1 << nbits[1]) == L["threads"]
     m = n.bit_length() - 1

@@ -1,0 +1,84 @@
+"""GPU parity of the swizzled in-place merge pass (32-bit keys without
+payload: tiles of 2^13 and 2^14 keys arrive by TMA tensor copies in the
+128-byte swizzled layout, every round works in place, bulk tensor stores
+write them back) against the oracle, bit-exact, both directions, through
+the device, host-buffer and sharded entry points."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import assert_equal, gpu_sort, total_order_u32
+
+pytestmark = pytest.mark.gpu
+
+# key kind, payload, log2 n, log2 tile, E (tile), E (window), window threads,
+# windows per pass, staging buffers (3: swizzled in place), forms, time,
+# shuffle stages
+_LINE = "0 0 {m} {t} 5 5 8 2 3 1 1 1 0.0 1"
+
+
+@pytest.fixture(params=[13, 14])
+def swz_tuned(darm, tmp_path, request):
+    t = request.param
+    db = str(tmp_path / f"swz{t}.db")
+    with open(db, "w") as f:
+        for m in range(t + 1, 27):
+            f.write(_LINE.format(m=m, t=t) + "\n")
+    darm.reset_tunings()
+    darm.load_tune_db(db)
+    yield darm, t
+    darm.reset_tunings()
+
+
+def _assert_swz_plan(darm, dtype, n, t):
+    merges = [L for L in darm.plan_dump(dtype, n, False, "melded",
+                                        tuning=(t, 5, 5, 8, 2, 3, 1)) if L["kind"] == 2]
+    assert merges and all(L["tma"] == 3 for L in merges), [L["tma"] for L in merges]
+
+
+@pytest.mark.parametrize("variant", ["divergent", "melded"])
+@pytest.mark.parametrize("m", [15, 17, 20, 22])
+@pytest.mark.parametrize("desc", [False, True])
+def test_keys_only(swz_tuned, m, variant, desc):
+    """Several tiles per CTA (2^22 keys: 256 or 512 tiles on 152 SMs, a
+    ragged last wave) and fewer tiles than SMs (2^15)."""
+    darm, t = swz_tuned
+    n = 1 << m
+    keys = synth.uniform_u32(1300 + m, n) % np.uint32(max(4, n // 8))
+    _assert_swz_plan(darm, darm.U32, n, t)
+    ek, _ = oracle.bitonic_sort(keys, None, desc=desc)
+    gk, _ = gpu_sort(darm, keys, None, desc=desc, variant=variant)
+    assert_equal("keys", gk, ek)
+
+
+@pytest.mark.parametrize("desc", [False, True])
+def test_float_keys_key_map_in_last_merge(swz_tuned, desc):
+    """The last merge pass undoes the float key map (and the descending
+    complement) before its bulk store."""
+    darm, t = swz_tuned
+    keys = synth.cfg3_f32(0xDA2C0003, 1 << 21)
+    _assert_swz_plan(darm, darm.F32, keys.size, t)
+    ek, _ = oracle.bitonic_sort(keys, None, desc=desc)
+    gk, _ = gpu_sort(darm, keys, None, desc=desc)
+    assert_equal("keys", total_order_u32(gk), total_order_u32(ek))
+
+
+def test_host_buffers(swz_tuned):
+    """Host-buffer sorts run the final stage's last merges per chunk: the
+    tensor map then covers one chunk from its own base."""
+    darm, t = swz_tuned
+    keys = synth.uniform_u32(0x5A11, 1 << 23)
+    ek, _ = oracle.bitonic_sort(keys, None)
+    hk = keys.copy()
+    darm.sort_host(hk)
+    assert_equal("keys", hk, ek)
+
+
+def test_default_plan_uses_it(darm):
+    """With tensor maps available the default plan of 2^26 keys runs its
+    merge passes in place (the full-size parity tests cover that plan)."""
+    darm.reset_tunings()
+    merges = [L for L in darm.plan_dump(darm.F32, 1 << 26, False, "melded") if L["kind"] == 2]
+    assert len(merges) == 12 and all(L["tma"] == 3 for L in merges)
+    assert darm.device_status() == 0

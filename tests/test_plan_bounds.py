@@ -41,7 +41,7 @@ def _tuner_candidates(hv):
         for e1 in (base_e1 - 1, base_e1):
             for e2 in (3, 4, 5):
                 for w2 in (1, 2):
-                    for tma in (0, 1, 2):
+                    for tma in (0, 1, 2, 3):
                         for shfl in (0, 1, 3):
                             yield (t, e1, e2, 8, w2, tma, shfl)
 
@@ -78,7 +78,7 @@ def test_plans_of_each_kernel_kind_are_covered():
         for L in darm.plan_dump(darm.U32, 1 << 18, False, "melded", tuning=tn):
             kinds.add(em.Kernel(L, 4, False).kind)
             mshfl = mshfl or bool(L["mshfl"])
-    assert {"tile_shfl", "tile_fixed", "tma_merge", "window1", "window2"} <= kinds, kinds
+    assert {"tile_shfl", "tile_fixed", "tma_merge", "swz_merge", "window1", "window2"} <= kinds, kinds
     assert mshfl, "no plan with the two-round shuffle merge"
 
 
@@ -104,3 +104,37 @@ def test_a_planted_off_by_one_is_caught(mutation):
         merge["rounds"][0]["p"] -= 1
     with pytest.raises(AssertionError):
         em.check_plan(bad, n, 4, True, full=True)
+
+
+@pytest.mark.parametrize("t", [13, 14])
+@pytest.mark.parametrize("mutation", ["none", "no_xor_round1", "row_bits_round2", "rounds"])
+def test_swizzled_merge_replay(t, mutation, monkeypatch):
+    """The swizzled in-place merge (keys only, tiles of 2^13 and 2^14): the
+    replay checks that the kernel's word offsets are the 128-byte swizzle of
+    the element each register holds in all three rounds; a planted mistake
+    in those offsets or in the plan's rounds fails it."""
+    n = 1 << 18
+    plan = darm.plan_dump(darm.U32, n, False, "melded", tuning=(t, 5, 5, 8, 2, 3, 1))
+    assert any(L["tma"] == 3 for L in plan), "no swizzled merge planned"
+    if mutation == "none":
+        em.check_plan(plan, n, 4, False, full=True)
+        return
+    if mutation == "rounds":
+        plan = [dict(L, rounds=[dict(R) for R in L["rounds"]]) for L in plan]
+        merge = next(L for L in plan if L["tma"] == 3)
+        merge["rounds"][0]["cnt"] -= 1
+        merge["rounds"][1]["cnt"] += 1
+        merge["rounds"][1]["a"] += 1
+    else:
+        good = em.swz_kernel_word
+
+        def bad(tid, r, rd, logt):
+            w = good(tid, r, rd, logt)
+            if mutation == "no_xor_round1" and rd == 1:
+                return ((tid >> 5) << 10) + (r << 5) + (tid & 31)
+            if mutation == "row_bits_round2" and rd == 2:
+                return (tid << 5) + (((r >> 2) ^ ((tid >> 1) & 7)) << 2) + (r & 3)
+            return w
+        monkeypatch.setattr(em, "swz_kernel_word", bad)
+    with pytest.raises(AssertionError):
+        em.check_plan(plan, n, 4, False, full=True)
