@@ -408,7 +408,9 @@ int darm_plan_info(int dtype, size_t n, int has_vals, int variant,
 
 /* Text description of the launch sequence darm_plan_info counts, one line
  * per launch: pass kind ("tile", "window", "merge"; "*" marks a
- * compile-time schedule, "~" a tile pass with shuffle stages), elements per
+ * compile-time schedule, "~" a tile pass with shuffle stages, "^" a pass
+ * that streams its blocks through shared memory with TMA tensor copies and
+ * works on them in place), elements per
  * thread, form, grid, threads, shared memory and the block bit map.  Writes
  * at most cap bytes into buf, NUL-terminated. */
 int darm_plan_describe(int dtype, size_t n, int has_vals, int variant, char* buf, size_t cap);
@@ -422,8 +424,10 @@ int darm_plan_describe(int dtype, size_t n, int has_vals, int variant, char* buf
  * passes).  smem_limit: shared
  * memory per block the plan may use (0: the device's, or 227 KiB before
  * init).  Writes, per launch, 21 int32 - pass kind (0 tile, 1 window,
- * 2 merge), compile-time tile/merge schedule, bulk-copy buffers, one-window
- * and two-window compile-time shapes, shuffle stages, log2 elements per
+ * 2 merge), compile-time tile/merge schedule, bulk-copy buffers (3: the
+ * keys-only merge in place in swizzled buffers), one-window and two-window
+ * compile-time shapes (two-window 2: streamed by TMA), shuffle stages,
+ * log2 elements per
  * thread, form, grid, threads, shared memory bytes, then the block bit map
  * b, c, w0, s, log2 of the array length, rounds, persistent block count,
  * key map in and out, two-round shuffle merge - followed by 7 int32 per

@@ -220,6 +220,7 @@ int batch_append(BatchTables& bt, KeyKind kk, bool has_vals, const Tuning& tn, i
     Launch L = L0;
     // the two-window and bulk-copy kernels address whole arrays only
     L.win2 = false;
+    L.win2t = false;
     L.win1 = false;
     L.tma = false;
     L.grid = uint32_t(bt.blocks.size() - bfirst);

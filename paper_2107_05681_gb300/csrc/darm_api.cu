@@ -51,6 +51,25 @@ static bool encode_key_rows(CUtensorMap* tm, void* keys, uint64_t rows, uint32_t
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor map of a two-window pass over `nblocks` blocks of 2^14 uint32 keys
+// from `keys`, window bits w0 .. w0+9: dimensions (16 consecutive keys, the
+// 2^(w0-4) positions between them and the windows, bottom window, top
+// window, the blocks above), one box = one block.
+static bool encode_window2_blocks(CUtensorMap* tm, void* keys, uint32_t nblocks, uint32_t w0) {
+  if (g_encode_tiled == nullptr || w0 < 4 || w0 + 12 > 40) return false;
+  const uint32_t nmid = w0 - 4;
+  if ((uint64_t(nblocks) & ((uint64_t(1) << nmid) - 1)) != 0) return false;
+  auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(g_encode_tiled);
+  const cuuint64_t dims[5] = {16, cuuint64_t(1) << nmid, 32, 32, cuuint64_t(nblocks) >> nmid};
+  const cuuint64_t strides[4] = {64, cuuint64_t(4) << w0, cuuint64_t(4) << (w0 + 5),
+                                 cuuint64_t(4) << (w0 + 10)};
+  const cuuint32_t box[5] = {16, 1, 32, 32, 1};
+  const cuuint32_t elem_strides[5] = {1, 1, 1, 1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT32, 5, keys, dims, strides, box, elem_strides,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_t* vals,
                 cudaStream_t stream, bool count) {
   const bool has_vals = vals != nullptr;
@@ -60,7 +79,8 @@ int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_
     P.vals = vals;
     P.status = g_ctx.d_status;
     const void* fn =
-        L.win1 ? window1_kernel(kk == KEY_U64, has_vals, L.loge, int(L.P.c)).fn
+        L.win2t ? window2_tma_kernel_u32(nullptr).fn
+        : L.win1 ? window1_kernel(kk == KEY_U64, has_vals, L.loge, int(L.P.c)).fn
         : L.win2 ? ((kk == KEY_U32) ? window2_kernel_u32(has_vals, L.loge, int(L.P.c), L.variant)
                                   : window2_kernel_u64(has_vals, L.loge, int(L.P.c), L.variant)).fn
         : L.mshfl ? tma_merge_shfl_kernel_u32(L.loge, int(L.P.b), L.tma, L.variant, nullptr).fn
@@ -72,6 +92,10 @@ int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_
     if (!fn) return DARM_ERR_INVALID_ARG;
     CUtensorMap tmap;
     void* args[] = {&P, &tmap};
+    if (L.win2t && !encode_window2_blocks(&tmap, keys, L.P.nblocks, L.P.w0)) {
+      fprintf(stderr, "darm: encoding the window pass's tensor map failed\n");
+      return DARM_ERR_CUDA;
+    }
     if (L.tma == 3) {
       // the tiles this launch covers, as rows of 32 keys from `keys`
       const int rows_log2 = int(L.P.b) - 5;
@@ -371,6 +395,9 @@ int sort_host_chunked(KeyKind kk, bool f32, void* keys_out, uint32_t* vals_out, 
     if (L.tma) {
       L.P.nblocks = uint32_t(1u << (mc - int(L.P.b)));
       L.grid = std::min(L.grid, L.P.nblocks);
+    } else if (L.win2t) {
+      L.P.nblocks >>= 3;  // 2^(m - b) blocks -> 2^(mc - b) per chunk
+      L.grid = std::min(L.grid, L.P.nblocks);
     } else {
       L.grid >>= 3;  // 2^(m - b) blocks -> 2^(mc - b) per chunk
     }
@@ -536,7 +563,7 @@ int darm_plan_dump(int dtype, size_t n, int has_vals, int variant, const int32_t
   if (!plan_array(plan, kk, hv, m, tn, variant, map, map, smem_limit)) return DARM_ERR_INVALID_ARG;
   std::vector<int32_t> v;
   for (const Launch& L : plan) {
-    const int32_t head[] = {int32_t(L.kind), L.fixed, L.tma, L.win1, L.win2, L.shfl, L.loge,
+    const int32_t head[] = {int32_t(L.kind), L.fixed, L.tma, L.win1, L.win2t ? 2 : int(L.win2), L.shfl, L.loge,
                             L.variant, int32_t(L.grid), int32_t(L.threads), int32_t(L.smem),
                             int32_t(L.P.b), int32_t(L.P.c), int32_t(L.P.w0), int32_t(L.P.s),
                             int32_t(L.P.log2cap), int32_t(L.P.nrounds), int32_t(L.P.nblocks),

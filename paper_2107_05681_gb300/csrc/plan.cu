@@ -342,6 +342,18 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
         KernelEntry w2e = (kk == KEY_U32) ? window2_kernel_u32(has_vals, e2, c, L.variant)
                                           : window2_kernel_u64(has_vals, e2, c, L.variant);
         L.win2 = (nr == 2 && w2e.fn != nullptr && int(L.threads) == w2e.max_threads);
+        // keys only, 32 keys per thread, 16 consecutive keys per block: the
+        // TMA-streamed form where tensor maps are available (tma mode 3)
+        size_t w2t_smem = 0;
+        if (L.win2 && tn.tma == 3 && g_tensor_maps != 0 && kk == KEY_U32 && !has_vals &&
+            e2 == 5 && c == 4 && rs[0].cnt == 5 &&
+            window2_tma_kernel_u32(&w2t_smem).fn != nullptr && w2t_smem <= smem_limit) {
+          L.win2 = false;
+          L.win2t = true;
+          L.smem = w2t_smem;
+          L.P.nblocks = L.grid;
+          L.grid = std::min<uint32_t>(L.grid, uint32_t(std::max(1, g_sms_for_plans)));
+        }
       }
       out.push_back(L);
       hi = lo - 1;
@@ -428,7 +440,7 @@ std::string describe(const std::vector<Launch>& plan) {
   std::ostringstream os;
   static const char* names[] = {"tile", "window", "merge"};
   for (const Launch& L : plan) {
-    os << names[L.kind] << (L.fixed ? "*" : "") << (L.shfl ? "~" : "") << " E=" << (1 << L.loge) << " var=" << L.variant << " grid=" << L.grid
+    os << names[L.kind] << (L.fixed ? "*" : "") << (L.shfl ? "~" : "") << (L.win2t || L.tma == 3 ? "^" : "") << " E=" << (1 << L.loge) << " var=" << L.variant << " grid=" << L.grid
        << " threads=" << L.threads << " smem=" << L.smem << " b=" << L.P.b << " c=" << L.P.c
        << " w0=" << L.P.w0 << " rounds=" << L.P.nrounds << "\n";
   }

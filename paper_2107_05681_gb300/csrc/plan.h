@@ -62,6 +62,8 @@ struct Launch {
                // (tma_merge_swz.cuh); 0: plain merge kernel
   bool win2;   // two-window pass with a compile-time shape (window2_kernel.cuh)
   bool win1;   // one-window pass with a compile-time shape (window1_kernel.cuh)
+  bool win2t;  // two-window pass streamed through shared memory by TMA
+               // (window2_tma.cuh): persistent over P.nblocks blocks
   bool shfl;   // tile pass with shuffle stages (tile_shfl_kernel.cuh)
   bool mshfl;  // bulk-copy merge in two rounds with shuffle layers
   int loge;

@@ -1,7 +1,10 @@
-// window2.cu - instantiations of the one- and two-window pass kernels.
+// window2.cu - instantiations of the one- and two-window pass kernels
+// (window1_kernel.cuh, window2_kernel.cuh) and of the two-window pass that
+// streams its blocks through shared memory with TMA (window2_tma.cuh).
 #include "kernel_table.h"
 #include "window1_kernel.cuh"
 #include "window2_kernel.cuh"
+#include "window2_tma.cuh"
 
 namespace darm {
 namespace {
@@ -46,7 +49,13 @@ KernelEntry window2_kernel_u64(bool has_vals, int loge, int c, int var) {
   return KernelEntry{nullptr, 0};
 }
 
+KernelEntry window2_tma_kernel_u32(size_t* smem_bytes) {
+  if (smem_bytes) *smem_bytes = W2tSmem::kBytes;
+  return KernelEntry{reinterpret_cast<const void*>(&darm_window2_tma_kernel), kW2tThreads};
+}
+
 void for_each_window2_kernel(void (*fn)(const void*, void*), void* ctx) {
+  fn(window2_tma_kernel_u32(nullptr).fn, ctx);
   for (int var = 0; var < 2; ++var) {
     fn(window2_kernel_u32(true, 4, 4, var).fn, ctx);
     fn(window2_kernel_u32(true, 4, 5, var).fn, ctx);

@@ -59,6 +59,26 @@ def swz_kernel_word(tid, r, rd, logt):
     return (tid << 5) + ((((r >> 2) ^ (tid & 7)) << 2) | (r & 3))
 
 
+def tma_box_global(L, blk, l):
+    """Global index of element l of block blk of a TMA two-window pass: the
+    tensor map's coordinates (16 consecutive keys, the w0 - 4 bits between
+    them and the windows, bottom window, top window, the bits above) with
+    the strides the host encodes (1, 16, 2^w0, 2^(w0+5), 2^(w0+10) keys)."""
+    w0 = L["w0"]
+    nmid = w0 - 4
+    mid = blk & ((1 << nmid) - 1)
+    high = blk >> nmid
+    d0, bw, tw = l & 15, (l >> 4) & 31, l >> 9
+    return d0 + 16 * mid + (bw << w0) + (tw << (w0 + 5)) + (high << (w0 + 10))
+
+
+def w2t_keeps_min_first(tid):
+    """Round 1's lowest layer in the TMA two-window kernel: register r of a
+    pair (r, r+1) takes the minimum (ascending) in lanes 0..15 and the
+    maximum in lanes 16..31 (keep_lo_first = asc != tw0)."""
+    return ((tid >> 4) & 1) == 0
+
+
 def check_swz_merge(K):
     """The swizzled merge runs a fixed schedule: it must be the plan's, and
     the kernel's own word offsets must be the swizzled slot of the element
@@ -92,8 +112,11 @@ class Kernel:
         self.kb = key_bytes
         self.hv = has_vals
         self.interleave = has_vals and key_bytes == 4
+        self.pair_swap = True  # window2_tma: round 1's register order in lanes 16..31
         if L["win1"]:
             self.kind = "window1"
+        elif L["win2"] == 2:
+            self.kind = "window2_tma"
         elif L["win2"]:
             self.kind = "window2"
         elif L["tma"] == 3:
@@ -117,6 +140,8 @@ class Kernel:
     def slot(self, l):
         if self.kind == "swz_merge":
             return swz128(l)
+        if self.kind == "window2_tma":
+            return l  # the tensor box, dense in local-index order
         if self.interleave:
             return phys8(l)
         if self.kind in ("tile_fixed", "tile_shfl", "window2"):
@@ -127,14 +152,19 @@ class Kernel:
         b = self.L["b"]
         if self.kind == "swz_merge":
             return 1 << b
+        if self.kind == "window2_tma":
+            return 1 << b
         if self.kind == "window2":
             b = self.L["c"] + 2 * self.loge
         return smem_words(1 << b)
 
     # -- the element a register holds: its index in the block (local) and in
     # the array (global)
-    def local(self, tid, r, a):
+    def local(self, tid, r, a, rd=None):
         tl = (tid & ((1 << a) - 1)) | ((tid >> a) << (a + self.loge))
+        if self.kind == "window2_tma" and rd == 1 and self.pair_swap:
+            # lanes 16..31 of a warp hold bottom-window position r ^ 1
+            r = r ^ ((tid >> 4) & 1)
         return tl | (r << a)
 
     def gblk(self, blk):
@@ -144,7 +174,7 @@ class Kernel:
         c, w0 = L["c"], L["w0"]
         nmid = w0 - c
         span = L["s"] if self.kind == "generic" else (
-            self.loge if self.kind == "window1" else 2 * self.loge)
+            self.loge if self.kind == "window1" else 2 * self.loge)  # window2, window2_tma
         return ((blk & ((1 << nmid) - 1)) << c) | ((blk >> nmid) << (w0 + span))
 
     def gmap(self, l):
@@ -159,7 +189,7 @@ class Kernel:
         L = self.L
         if self.kind == "window1":
             return L["c"]
-        if self.kind == "window2":
+        if self.kind in ("window2", "window2_tma"):
             return L["c"] + self.loge if rd == 0 else L["c"]
         return L["rounds"][rd]["a"]
 
@@ -170,6 +200,8 @@ class Kernel:
         gb = self.gblk(blk)
         if self.kind == "window1":
             return (tid | gb) + (r << L["w0"])
+        if self.kind == "window2_tma":
+            return tma_box_global(L, blk, self.local(tid, r, a, rd))
         if self.kind == "window2":
             tl = (tid & ((1 << a) - 1)) | ((tid >> a) << (a + self.loge))
             c = L["c"]
@@ -193,7 +225,7 @@ class Kernel:
             1 if self.kind == "window1" else 2)
         if self.kind == "window1":
             return True
-        if self.kind == "window2":
+        if self.kind in ("window2", "window2_tma"):
             return True
         R = L["rounds"][rd]
         last = rd + 1 == nr
@@ -202,7 +234,7 @@ class Kernel:
     def nrounds(self):
         if self.kind == "window1":
             return 1
-        if self.kind == "window2":
+        if self.kind in ("window2", "window2_tma"):
             return 2
         return len(self.L["rounds"])
 
@@ -214,41 +246,49 @@ class Kernel:
             # _check_layers on the consecutive layout
             return L["rounds"][0]["p"], []
         R = L["rounds"][rd] if self.kind not in ("window1",) else L["rounds"][0]
-        if self.kind == "window2":
+        if self.kind in ("window2", "window2_tma"):
             R = L["rounds"][rd]
         if self.kind in ("tma_merge", "swz_merge") or (self.kind == "tile_fixed" and L["kind"] == MERGE):
             p = L["rounds"][0]["p"]
         else:
             p = R["p"]
-        cnt = E.bit_length() - 1 if (self.kind == "window2" and rd == 0) else R["cnt"]
+        cnt = E.bit_length() - 1 if (self.kind in ("window2", "window2_tma") and rd == 0) else R["cnt"]
         return p, [self.loge - 1 - i for i in range(cnt)]
 
 
 def _grid_arrays(K):
     L = K.L
-    blocks = L["nblocks"] if K.kind in ("tma_merge", "swz_merge") else L["grid"]
+    blocks = L["nblocks"] if K.kind in ("tma_merge", "swz_merge", "window2_tma") else L["grid"]
     blk = np.arange(blocks, dtype=np.int64)[:, None, None]
     tid = np.arange(L["threads"], dtype=np.int64)[None, :, None]
     r = np.arange(K.E, dtype=np.int64)[None, None, :]
     return blk, tid, r
 
 
-def check_launch_full(K, n, seq):
-    """Enumerate every (block, thread, register) of every round."""
+def check_launch_full(K, n, seq, blocks=None):
+    """Enumerate every (block, thread, register) of every round.  `blocks`:
+    only these blocks (their elements distinct and in range; the bijection
+    onto [0, n) is then left to check_launch_linear)."""
     blk, tid, r = _grid_arrays(K)
+    if blocks is not None:
+        blk = np.asarray(blocks, dtype=np.int64)[:, None, None]
     if K.kind == "swz_merge":
         check_swz_merge(K)
     for rd in range(K.nrounds()):
         a = K.window_of(rd)
-        l = K.local(tid, r, a) + 0 * blk
+        l = K.local(tid, r, a, rd) + 0 * blk
         g = K.gmap(l) | K.gblk(blk)
         flat = g.reshape(-1)
         assert flat.min() >= 0 and flat.max() < n, (K.kind, rd, "element index out of range")
-        assert np.unique(flat).size == flat.size == n, (K.kind, rd, "not a bijection onto [0, n)")
+        if blocks is None:
+            assert np.unique(flat).size == flat.size == n, (K.kind, rd, "not a bijection onto [0, n)")
+        else:
+            assert np.unique(flat).size == flat.size, (K.kind, rd, "an element taken twice")
         if K.touches_hbm(rd):
             h = K.hbm_address(blk, tid, r, rd) + 0 * g
             assert np.array_equal(h, g), (K.kind, rd, "HBM address differs from the element")
-        if K.kind in ("tile_fixed", "tile_shfl", "tma_merge", "swz_merge", "window2", "generic") and (
+        if K.kind in ("tile_fixed", "tile_shfl", "tma_merge", "swz_merge", "window2", "window2_tma",
+                      "generic") and (
                 K.kind != "generic" or K.L["smem"] > 0) and K.kind != "window1":
             s = K.slot(l)
             assert s.min() >= 0 and s.max() < K.slot_bound(), (K.kind, rd, "slot out of range")
@@ -293,6 +333,14 @@ def _check_layers(K, rd, g, seq):
         lo = g[..., [r for r in range(K.E) if not (r >> q) & 1]]
         hi = g[..., [r | (1 << q) for r in range(K.E) if not (r >> q) & 1]]
         d = hi - lo
+        if K.kind == "window2_tma" and rd == 1 and q == 0 and K.pair_swap:
+            # the pair-swapped lanes hold the higher index first; the kernel
+            # must give the minimum to whichever register holds the lower one
+            tid = np.arange(K.L["threads"], dtype=np.int64)[None, :, None]
+            first_is_lower = (d > 0)
+            assert np.all(first_is_lower == w2t_keeps_min_first(tid)), \
+                (K.kind, rd, "pair-swapped layer keeps min and max on the wrong registers")
+            d = np.abs(d)
         bit = int(d.reshape(-1)[0])
         assert bit > 0 and bit & (bit - 1) == 0 and np.all(d == bit), \
             (K.kind, rd, "layer pairs do not differ in one bit")
@@ -319,9 +367,12 @@ def check_plan(plan, n, key_bytes, has_vals, full=True, rng=None):
 
 def check_launch_linear(K, n, seq, rng):
     """Large arrays: the maps are ORs of shifted bit fields; check them on
-    single bits and random samples instead of enumerating."""
+    single bits and random samples instead of enumerating.  (The TMA
+    two-window pass's register order within a thread, a relabelling that
+    keeps every bound and bijection, is checked by the full replay.)"""
     L = K.L
-    blocks = L["nblocks"] if K.kind in ("tma_merge", "swz_merge") else L["grid"]
+    K.pair_swap = False
+    blocks = L["nblocks"] if K.kind in ("tma_merge", "swz_merge", "window2_tma") else L["grid"]
     if K.kind == "swz_merge":
         check_swz_merge(K)
     nbits = [blocks.bit_length() - 1, L["threads"].bit_length() - 1, K.loge]

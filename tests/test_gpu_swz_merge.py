@@ -1,8 +1,10 @@
-"""GPU parity of the swizzled in-place merge pass (32-bit keys without
-payload: tiles of 2^13 and 2^14 keys arrive by TMA tensor copies in the
-128-byte swizzled layout, every round works in place, bulk tensor stores
-write them back) against the oracle, bit-exact, both directions, through
-the device, host-buffer and sharded entry points."""
+"""GPU parity of the passes that stream 32-bit keys (no payload) through
+shared memory with TMA tensor copies and work on them in place: the
+swizzled merge pass (tiles of 2^13 and 2^14 keys in the 128-byte swizzled
+layout) and the two-window pass (blocks of 16 consecutive keys x 2 windows
+of 5 bits, round 1 pair-swapped in half of each warp), against the oracle,
+bit-exact, both directions, through the device and host-buffer entry
+points."""
 import numpy as np
 import pytest
 
@@ -81,4 +83,29 @@ def test_default_plan_uses_it(darm):
     darm.reset_tunings()
     merges = [L for L in darm.plan_dump(darm.F32, 1 << 26, False, "melded") if L["kind"] == 2]
     assert len(merges) == 12 and all(L["tma"] == 3 for L in merges)
+    assert darm.device_status() == 0
+
+
+@pytest.mark.parametrize("desc", [False, True])
+@pytest.mark.parametrize("dtype", ["u32", "f32"])
+def test_tma_two_window_passes(darm, desc, dtype):
+    """2^24 keys with the default plan: two-window passes of six to ten
+    layers streamed by TMA (the ten-layer one runs the pair-swapped lowest
+    layer), swizzled merges."""
+    darm.reset_tunings()
+    n = 1 << 24
+    code = darm.U32 if dtype == "u32" else darm.F32
+    plan = darm.plan_dump(code, n, False, "melded")
+    w2t = [L for L in plan if L["win2"] == 2]
+    assert w2t and any(L["rounds"][1]["cnt"] == 5 for L in w2t), [L["win2"] for L in plan]
+    if dtype == "u32":
+        keys = synth.uniform_u32(0x2A0E, n) % np.uint32(n // 4)
+        ek, _ = oracle.bitonic_sort(keys, None, desc=desc)
+        gk, _ = gpu_sort(darm, keys, None, desc=desc)
+        assert_equal("keys", gk, ek)
+    else:
+        keys = synth.cfg3_f32(0xDA2C0003, n)
+        ek, _ = oracle.bitonic_sort(keys, None, desc=desc)
+        gk, _ = gpu_sort(darm, keys, None, desc=desc)
+        assert_equal("keys", total_order_u32(gk), total_order_u32(ek))
     assert darm.device_status() == 0
