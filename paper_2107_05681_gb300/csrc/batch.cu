@@ -42,12 +42,19 @@ Tuning batch_tuning(KeyKind kk, bool has_vals, int cmax) {
     std::lock_guard<std::mutex> lk(g_ctx.mu);
     tuned = g_ctx.tuned.count(std::make_tuple(int(kk), int(has_vals), 0)) != 0;
   }
-  // Untuned 32-bit key-value batches take 8 Ki-pair tiles: their merge passes
-  // run the table-driven kernel (no bulk-copy prefetch), and there the larger
-  // tile's saved sweeps win (10,000 segments of up to 2^16 pairs: 4.92 ->
-  // 4.52 ms against 4 Ki-pair tiles).
+  // Untuned 32-bit key-value batches take 8 Ki-pair tiles (10,000 segments
+  // of up to 2^16 pairs: 4.92 -> 4.52 ms against 4 Ki-pair tiles, when the
+  // merge passes ran the table-driven tile kernel).
   if (!tuned && kk == KEY_U32 && has_vals) tn.t = 13;
-  tn.tma = 0;  // batch passes resolve every block through a table
+  // tma: staging buffers of the bulk-copy merge, which reads each tile's
+  // place from the block table (0: the table-driven tile kernel; no
+  // swizzled in-place form for batches)
+  if (kk != KEY_U32)
+    tn.tma = 0;
+  else if (!tuned)
+    tn.tma = has_vals ? 1 : 2;
+  else
+    tn.tma = std::min(tn.tma, 2);
   fit_tuning(tn, kk, has_vals, std::max(cmax, tn.t), g_ctx.smem_limit);
   return tn;
 }
@@ -200,7 +207,9 @@ int batch_append(BatchTables& bt, KeyKind kk, bool has_vals, const Tuning& tn, i
   std::vector<uint32_t> sl(act.size());
   for (size_t j = 0; j < act.size(); ++j) sl[j] = add_slot(*act[j]);
   std::vector<Launch> shape;
-  if (!plan_array(shape, kk, has_vals, p, tn, variant, 0, 0, g_ctx.smem_limit))
+  Tuning tp = tn;
+  tp.tma = 0;  // the whole-array shapes; merges are given the bulk-copy kernel below
+  if (!plan_array(shape, kk, has_vals, p, tp, variant, 0, 0, g_ctx.smem_limit))
     return DARM_ERR_INVALID_ARG;
   for (const Launch& L0 : shape) {
     if (L0.kind == PASS_TILE || L0.P.rounds[0].p != p) continue;
@@ -218,12 +227,32 @@ int batch_append(BatchTables& bt, KeyKind kk, bool has_vals, const Tuning& tn, i
       }
     }
     Launch L = L0;
-    // the two-window and bulk-copy kernels address whole arrays only
+    // the window kernels with compile-time shapes address whole arrays only
     L.win2 = false;
     L.win2t = false;
     L.win1 = false;
-    L.tma = false;
+    L.tma = 0;
+    L.mshfl = false;
     L.grid = uint32_t(bt.blocks.size() - bfirst);
+    size_t tma_smem = 0;
+    if (L0.kind == PASS_MERGE && kk == KEY_U32 && (tn.tma == 1 || tn.tma == 2)) {
+      // merge blocks are whole tiles of one segment: the persistent
+      // bulk-copy merge streams them in, finding each in the table
+      const KernelEntry te = tma_merge_kernel_u32(has_vals, L0.loge, t, tn.tma, L.variant, &tma_smem);
+      if (te.fn != nullptr && tma_smem <= g_ctx.smem_limit && int(L.threads) == te.max_threads) {
+        int per_sm = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, te.fn, int(L.threads), tma_smem) !=
+                cudaSuccess ||
+            per_sm < 1) {
+          cudaGetLastError();
+          per_sm = 1;
+        }
+        L.tma = tn.tma;
+        L.smem = tma_smem;
+        L.P.nblocks = L.grid;
+        L.grid = std::min<uint32_t>(L.grid, uint32_t(std::max(1, g_ctx.sms) * per_sm));
+      }
+    }
     L.P.log2cap = 0;
     L.P.map_in = map_in;
     L.P.map_out = 0;

@@ -181,7 +181,8 @@ uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
 // Every field of a tuning that changes a batch's launches.
 uint64_t tuning_key(const Tuning& tn) {
   uint64_t k = 0;
-  for (int v : {tn.t, tn.e1, tn.e2, tn.c2, tn.w2, tn.tma, tn.var[0], tn.var[1], tn.var[2]})
+  for (int v : {tn.t, tn.e1, tn.e2, tn.c2, tn.w2, tn.tma, tn.shfl, tn.em, tn.var[0], tn.var[1],
+                tn.var[2]})
     k = k * 64 + uint64_t(v & 63);
   return k;
 }
@@ -297,7 +298,6 @@ extern "C" int darm_autotune_segmented(uint32_t* keys, uint32_t* vals, const uin
   // the tuning cannot run this layout
   auto time_tuning = [&](const Tuning& tn0) -> float {
     Tuning tn = tn0;
-    tn.tma = 0;
     if (!fit_tuning(tn, KEY_U32, hv, std::max(cmax, tn.t), g_ctx.smem_limit)) return -1.f;
     SegPlan sp;
     if (build_seg_plan(sp, keys, vals, segs, DARM_AUTO, tn) != DARM_OK) {
@@ -320,14 +320,18 @@ extern "C" int darm_autotune_segmented(uint32_t* keys, uint32_t* vals, const uin
   const Tuning base = default_tuning(KEY_U32, hv);
   Tuning best = base;
   float best_ms = -1.f;
+  // merge passes: the table-driven tile kernel (0) or the bulk-copy merge
+  // with its staging buffers (1 for key-value, 2 for keys)
+  const int tma_on = hv ? 1 : 2;
   for (int t = base.t - 1; t <= base.t + 1; ++t)
     for (int e2 = 3; e2 <= 5; ++e2)
-      for (int w2 = 1; w2 <= 2; ++w2) {
+      for (int w2 = 1; w2 <= 2; ++w2)
+      for (int tma : {0, tma_on}) {
         Tuning tn = base;
         tn.t = t;
         tn.e2 = e2;
         tn.w2 = w2;
-        tn.tma = 0;
+        tn.tma = tma;
         tn.var[0] = tn.var[1] = tn.var[2] = kMelded;
         const float ms = time_tuning(tn);
         if (ms >= 0.f && (best_ms < 0.f || ms < best_ms)) {

@@ -126,17 +126,35 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_ke
   uint32_t* __restrict__ gv = P.vals;
   const uint32_t tid = threadIdx.x;
   const uint32_t ntiles = P.nblocks;
-  const uint32_t capmask = (1u << P.log2cap) - 1u;
   const uint32_t p = P.rounds[0].p;
   constexpr uint32_t kBytes = uint32_t(L::kStage);
 
+  // Tile `tl` of this launch: its first element in the arrays, the index
+  // its comparator directions are taken from, the capacity mask of the
+  // sequence it belongs to and the key map its last store undoes.  Whole
+  // arrays: tile tl of the array.  Batches: entry tl of the block table, a
+  // tile of one segment (merge blocks never pack several segments).
+  struct TileAt {
+    size_t start;
+    uint32_t dir_idx, capmask, mout;
+  };
+  auto tile_at = [&](uint32_t tl) -> TileAt {
+    if (P.blocks == nullptr)
+      return TileAt{size_t(tl) << LOGT, (tl << LOGT) | P.dir_base, (1u << P.log2cap) - 1u, P.map_out};
+    const SegBlock B = P.blocks[tl];
+    const SegSlot S = P.slots[B.first_slot];
+    const uint32_t f = P.map_in | ((S.flags & kSlotDesc) ? kMapComplement : 0u);
+    return TileAt{size_t(S.base) + (size_t(B.blk_in_seg) << LOGT), B.blk_in_seg << LOGT,
+                  (1u << B.log2cap) - 1u, B.final_pass ? f : 0u};
+  };
   // copy tile `tl` into staging buffer `b` (thread 0 only)
   auto issue = [&](uint32_t tl, int b) {
     const uint32_t bar = bar0 + 8u * uint32_t(b);
     unsigned char* st = smem_raw + size_t(b) * L::kStage;
+    const size_t start = tile_at(tl).start;
     mbar_expect_tx(bar, kBytes);
-    bulk_g2s(smem_addr(st), gk + size_t(tl) * L::kTile, uint32_t(L::kStageK), bar);
-    if (V) bulk_g2s(smem_addr(st + L::kStageK), gv + size_t(tl) * L::kTile, uint32_t(L::kStageV), bar);
+    bulk_g2s(smem_addr(st), gk + start, uint32_t(L::kStageK), bar);
+    if (V) bulk_g2s(smem_addr(st + L::kStageK), gv + start, uint32_t(L::kStageV), bar);
   };
 
   uint32_t tile = blockIdx.x;
@@ -183,8 +201,10 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_ke
     pending &= ~(1u << b);
     const K* stage_k = reinterpret_cast<const K*>(smem_raw + size_t(b) * L::kStage);
     const uint32_t* stage_v = reinterpret_cast<const uint32_t*>(smem_raw + size_t(b) * L::kStage + L::kStageK);
-    const uint32_t gblk = tile << LOGT;
-    const bool asc = (((gblk | P.dir_base) & (1u << p) & capmask) == 0u);
+    const TileAt at = tile_at(tile);
+    K* const tk = gk + at.start;
+    uint32_t* const tv = V ? gv + at.start : nullptr;
+    const bool asc = ((at.dir_idx & (1u << p) & at.capmask) == 0u);
     const uint32_t next = tile + uint32_t(NS) * gridDim.x;
 
     if constexpr (SH) {
@@ -196,7 +216,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_ke
 #pragma unroll
           for (int r = 0; r < E; ++r) kr[r] = stage_k[tl | (uint32_t(r) << A0)];
           window_side<K, V, LOGE, ASC, true>(kr, vr, LOGE);
-          s_store<K, V, LOGE, A0, false, true>(kr, vr, false, gk, gv, 0u, sk, sv, phys(tl), 0u, K(0));
+          s_store<K, V, LOGE, A0, false, true>(kr, vr, false, tk, tv, 0u, sk, sv, phys(tl), 0u, K(0));
         };
         if (asc)
           body(std::true_type{});
@@ -215,7 +235,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_ke
         // round 1: E consecutive keys per thread; lane bits are index bits
         // LOGE .. LOGE+4
         const uint32_t tl = tid << LOGE;
-        s_load<K, V, LOGE, 0, false>(kr, vr, false, gk, gv, 0u, sk, sv, phys(tl), 0u, K(0));
+        s_load<K, V, LOGE, 0, false>(kr, vr, false, tk, tv, 0u, sk, sv, phys(tl), 0u, K(0));
 #pragma unroll
         for (int q = A0 - 1; q >= LOGE; --q)
           merge_shfl_layer<K, LOGE, 0xFFFFFFFFu>(kr, 1u << (q - LOGE), asc);
@@ -223,8 +243,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_ke
           window_side<K, V, LOGE, true, true>(kr, vr, LOGE);
         else
           window_side<K, V, LOGE, false, true>(kr, vr, LOGE);
-        s_store<K, V, LOGE, 0, false, true>(kr, vr, true, gk, gv, tl | gblk, sk, sv, 0u, P.map_out,
-                                            K(0));
+        s_store<K, V, LOGE, 0, false, true>(kr, vr, true, tk, tv, tl, sk, sv, 0u, at.mout, K(0));
       }
       __syncthreads();
       b = (b + 1 == NS) ? 0 : b + 1;
@@ -236,9 +255,9 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_ke
       constexpr int A = R.a;
       constexpr bool LAST = (IDX + 1 == NR);
       const uint32_t tl = (tid & ((1u << A) - 1u)) | ((tid >> A) << (A + LOGE));
-      const uint32_t g_full = tl | gblk;
+      const uint32_t g_full = tl;  // relative to the tile's first element
       const uint32_t s_base = Interleave<K, V>::value ? phys8(tl) : phys(tl);
-      const uint32_t mout = LAST ? P.map_out : 0u;
+      const uint32_t mout = LAST ? at.mout : 0u;
       if constexpr (IDX == 0) {
         // from the dense staging buffer into the padded work buffer
         auto body = [&](auto asc_c) {
@@ -250,7 +269,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_ke
             if (V) vr[r] = stage_v[l];
           }
           window_side<K, V, LOGE, ASC, true>(kr, vr, R.cnt);
-          s_store<K, V, LOGE, A, false, true>(kr, vr, LAST, gk, gv, g_full, sk, sv, s_base, mout, K(0));
+          s_store<K, V, LOGE, A, false, true>(kr, vr, LAST, tk, tv, g_full, sk, sv, s_base, mout, K(0));
         };
         if (asc)
           body(std::true_type{});
@@ -268,13 +287,13 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256) ? 4 : 1) darm_merge_tma_ke
         }
       } else {
         if (asc) {
-          s_load<K, V, LOGE, A, false>(kr, vr, false, gk, gv, g_full, sk, sv, s_base, 0u, K(0));
+          s_load<K, V, LOGE, A, false>(kr, vr, false, tk, tv, g_full, sk, sv, s_base, 0u, K(0));
           window_side<K, V, LOGE, true, true>(kr, vr, R.cnt);
-          s_store<K, V, LOGE, A, false, true>(kr, vr, LAST, gk, gv, g_full, sk, sv, s_base, mout, K(0));
+          s_store<K, V, LOGE, A, false, true>(kr, vr, LAST, tk, tv, g_full, sk, sv, s_base, mout, K(0));
         } else {
-          s_load<K, V, LOGE, A, true>(kr, vr, false, gk, gv, g_full, sk, sv, s_base, 0u, K(0));
+          s_load<K, V, LOGE, A, true>(kr, vr, false, tk, tv, g_full, sk, sv, s_base, 0u, K(0));
           window_side<K, V, LOGE, false, true>(kr, vr, R.cnt);
-          s_store<K, V, LOGE, A, true, true>(kr, vr, LAST, gk, gv, g_full, sk, sv, s_base, mout, K(0));
+          s_store<K, V, LOGE, A, true, true>(kr, vr, LAST, tk, tv, g_full, sk, sv, s_base, mout, K(0));
         }
         __syncthreads();
       }
