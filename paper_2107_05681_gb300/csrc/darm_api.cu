@@ -90,17 +90,19 @@ int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_
         : L.fixed ? fixed_kernel_fn(kk, has_vals, L.loge, int(L.P.b), L.variant, L.kind == PASS_MERGE)
                   : kernel_fn(kk, has_vals, L.loge, L.variant);
     if (!fn) return DARM_ERR_INVALID_ARG;
-    CUtensorMap tmap;
-    void* args[] = {&P, &tmap};
+    CUtensorMap tmap, tmap2;
+    void* args[] = {&P, &tmap, &tmap2};
     if (L.win2t && !encode_window2_blocks(&tmap, keys, L.P.nblocks, L.P.w0)) {
       fprintf(stderr, "darm: encoding the window pass's tensor map failed\n");
       return DARM_ERR_CUDA;
     }
     if (L.tma == 3) {
-      // the tiles this launch covers, as rows of 32 keys from `keys`
+      // the tiles this launch covers, as rows of 32 keys (and payloads)
       const int rows_log2 = int(L.P.b) - 5;
       const uint64_t rows = uint64_t(L.P.nblocks) << rows_log2;
-      if (!encode_key_rows(&tmap, keys, rows, rows_log2 >= 8 ? 256u : (1u << rows_log2))) {
+      const uint32_t box = rows_log2 >= 8 ? 256u : (1u << rows_log2);
+      if (!encode_key_rows(&tmap, keys, rows, box) ||
+          (has_vals && !encode_key_rows(&tmap2, vals, rows, box))) {
         fprintf(stderr, "darm: encoding the merge pass's tensor map failed\n");
         return DARM_ERR_CUDA;
       }

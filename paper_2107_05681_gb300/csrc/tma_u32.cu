@@ -1,7 +1,7 @@
 // tma_u32.cu - instantiations of the bulk-copy-prefetching merge passes for
 // uint32_t keys: dense staging buffers (tma_merge.cuh, 1 or 2 buffers) and
 // the in-place swizzled form with bulk tensor stores (tma_merge_swz.cuh,
-// "3 buffers", keys only).
+// "3 buffers": keys alone, or keys with a payload in two buffer halves).
 #include "kernel_table.h"
 #include "tma_merge.cuh"
 #include "tma_merge_swz.cuh"
@@ -28,6 +28,12 @@ KernelEntry swz_entry(size_t* smem_bytes) {
   return KernelEntry{reinterpret_cast<const void*>(&darm_merge_swz_kernel<LOGT>), 1 << (LOGT - 5)};
 }
 
+template <int LOGT>
+KernelEntry swz_kv_entry(size_t* smem_bytes) {
+  if (smem_bytes) *smem_bytes = SwzKvSmem<LOGT>::kBytes;
+  return KernelEntry{reinterpret_cast<const void*>(&darm_merge_swz_kv_kernel<LOGT>), 1 << (LOGT - 4)};
+}
+
 template <bool V, int LOGE, int LOGT>
 KernelEntry mpick(int ns, int var, size_t* smem_bytes) {
   if (ns == 1) return mentry<V, LOGE, LOGT, 1>(var, smem_bytes);
@@ -48,6 +54,8 @@ KernelEntry tma_merge_kernel_u32(bool has_vals, int loge, int logt, int ns, int 
   if (ns == 3) {  // one form: the direction is uniform per tile
     if (!has_vals && loge == 5 && logt == 14) return swz_entry<14>(smem_bytes);
     if (!has_vals && loge == 5 && logt == 13) return swz_entry<13>(smem_bytes);
+    if (has_vals && loge == 4 && logt == 12) return swz_kv_entry<12>(smem_bytes);
+    if (has_vals && loge == 4 && logt == 13) return swz_kv_entry<13>(smem_bytes);
     return KernelEntry{nullptr, 0};
   }
   if (has_vals && loge == 4 && logt == 12) return mpick<true, 4, 12>(ns, var, smem_bytes);
@@ -69,6 +77,8 @@ void for_each_tma_kernel_u32(void (*fn)(const void*, void*), void* ctx) {
     }
   fn(tma_merge_kernel_u32(false, 5, 14, 3, 0, nullptr).fn, ctx);
   fn(tma_merge_kernel_u32(false, 5, 13, 3, 0, nullptr).fn, ctx);
+  fn(tma_merge_kernel_u32(true, 4, 12, 3, 0, nullptr).fn, ctx);
+  fn(tma_merge_kernel_u32(true, 4, 13, 3, 0, nullptr).fn, ctx);
   for (int var = 0; var < 2; ++var) {
     fn(tma_merge_shfl_kernel_u32(5, 14, 2, var, nullptr).fn, ctx);
     fn(tma_merge_shfl_kernel_u32(5, 13, 2, var, nullptr).fn, ctx);

@@ -69,10 +69,10 @@ __global__ void __launch_bounds__(kW2tThreads, 1)
   using K = uint32_t;
   constexpr int E = 32;
   constexpr uint32_t kBlockB = W2tSmem::kBlockBytes;
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  const uint32_t sraw = smem_addr(smem_raw);
+  extern __shared__ __align__(1024) unsigned char w2t_smem[];
+  const uint32_t sraw = smem_addr(w2t_smem);
   const uint32_t sbase = (sraw + 1023u) & ~1023u;
-  unsigned char* sbuf = smem_raw + (sbase - sraw);
+  unsigned char* sbuf = w2t_smem + (sbase - sraw);
   const uint32_t bar0 = sbase + uint32_t(kSwzBuffers) * kBlockB;
   const uint32_t tid = threadIdx.x;
   const uint32_t nblocks = P.nblocks;

@@ -79,10 +79,61 @@ def w2t_keeps_min_first(tid):
     return ((tid >> 4) & 1) == 0
 
 
+def swz_kv_kernel_word(tid, r, a):
+    """The word offsets the key-value in-place merge kernel computes
+    (tma_merge_swz.cuh) for register r of thread tid in the round whose
+    window sits at bit a (keys and payloads alike)."""
+    if a >= 8:
+        tl = (tid & ((1 << a) - 1)) | ((tid >> a) << (a + 4))
+        return (tl ^ (((tl >> 5) & 7) << 2)) + (r << a)
+    if a == 4:
+        tl = (tid & 15) | ((tid >> 4) << 8)
+        flip = (tid >> 4) & 1
+        base = tl | (((r & 1) ^ flip) << 4)
+        return (base ^ (((r >> 1) & 7) << 2)) + ((r >> 1) << 5)
+    assert a == 0
+    c = ((((tid & 1) << 2) | (r >> 2)) ^ ((tid >> 1) & 7)) << 2
+    return ((tid >> 1) << 5) + c + (r & 3)
+
+
+def swz_kv_first_is_lower(tid):
+    """The key-value merge's lowest layer of the window at bit 4: register r
+    of a pair (r, r+1) holds the lower index in lanes 0..15 (the kernel's
+    `flip` is lane >> 4)."""
+    return ((tid & 31) >> 4) == 0
+
+
+def check_swz_kv_merge(K):
+    L = K.L
+    b = L["b"]
+    assert K.loge == 4 and b in (12, 13) and K.hv and K.kb == 4, "key-value swizzled merge shape"
+    assert L["threads"] == 1 << (b - 4)
+    exp = []
+    for i in range((b + 3) // 4 - 1, -1, -1):
+        hi = min((i + 1) * 4, b) - 1
+        exp.append((hi - 3, hi - i * 4 + 1))
+    got = [(R["a"], R["cnt"]) for R in L["rounds"]]
+    assert got == exp, ("key-value swizzled merge rounds", got, exp)
+    tid = np.arange(L["threads"], dtype=np.int64)[:, None]
+    r = np.arange(16, dtype=np.int64)[None, :]
+    saved, K.pair_swap = K.pair_swap, True  # the kernel's own register order
+    try:
+        for rd, (a, _) in enumerate(got):
+            l = K.local(tid, r, a, rd)
+            w = swz_kv_kernel_word(tid, r, a)
+            assert np.array_equal(w, swz128(l)), ("key-value swizzled word offsets", rd)
+            assert w.min() >= 0 and w.max() < (1 << b) and np.unique(w).size == w.size
+    finally:
+        K.pair_swap = saved
+
+
 def check_swz_merge(K):
     """The swizzled merge runs a fixed schedule: it must be the plan's, and
     the kernel's own word offsets must be the swizzled slot of the element
     the register holds, in every round (the rounds work in place)."""
+    if K.hv:
+        check_swz_kv_merge(K)
+        return
     L = K.L
     b = L["b"]
     assert K.loge == 5 and b in (13, 14) and not K.hv and K.kb == 4, "swizzled merge shape"
@@ -112,7 +163,7 @@ class Kernel:
         self.kb = key_bytes
         self.hv = has_vals
         self.interleave = has_vals and key_bytes == 4
-        self.pair_swap = True  # window2_tma: round 1's register order in lanes 16..31
+        self.pair_swap = True  # round-1 / bit-4 register order in lanes 16..31 (TMA kernels)
         if L["win1"]:
             self.kind = "window1"
         elif L["win2"] == 2:
@@ -164,6 +215,9 @@ class Kernel:
         tl = (tid & ((1 << a) - 1)) | ((tid >> a) << (a + self.loge))
         if self.kind == "window2_tma" and rd == 1 and self.pair_swap:
             # lanes 16..31 of a warp hold bottom-window position r ^ 1
+            r = r ^ ((tid >> 4) & 1)
+        if self.kind == "swz_merge" and self.hv and a == 4 and self.pair_swap:
+            # key-value merge, window at bit 4: the same swap
             r = r ^ ((tid >> 4) & 1)
         return tl | (r << a)
 
@@ -333,6 +387,11 @@ def _check_layers(K, rd, g, seq):
         lo = g[..., [r for r in range(K.E) if not (r >> q) & 1]]
         hi = g[..., [r | (1 << q) for r in range(K.E) if not (r >> q) & 1]]
         d = hi - lo
+        if K.kind == "swz_merge" and K.hv and K.window_of(rd) == 4 and q == 0 and K.pair_swap:
+            tid = np.arange(K.L["threads"], dtype=np.int64)[None, :, None]
+            assert np.all((d > 0) == swz_kv_first_is_lower(tid)), \
+                (K.kind, rd, "pair-swapped layer keeps min and max on the wrong registers")
+            d = np.abs(d)
         if K.kind == "window2_tma" and rd == 1 and q == 0 and K.pair_swap:
             # the pair-swapped lanes hold the higher index first; the kernel
             # must give the minimum to whichever register holds the lower one

@@ -109,3 +109,50 @@ def test_tma_two_window_passes(darm, desc, dtype):
         gk, _ = gpu_sort(darm, keys, None, desc=desc)
         assert_equal("keys", total_order_u32(gk), total_order_u32(ek))
     assert darm.device_status() == 0
+
+
+_KV = "0 1 {m} {t} 4 4 8 2 3 1 1 1 0.0 1"
+
+
+@pytest.fixture(params=[12, 13])
+def swz_kv_tuned(darm, tmp_path, request):
+    t = request.param
+    db = str(tmp_path / f"swzkv{t}.db")
+    with open(db, "w") as f:
+        for m in range(t + 1, 27):
+            f.write(_KV.format(m=m, t=t) + "\n")
+    darm.reset_tunings()
+    darm.load_tune_db(db)
+    yield darm, t
+    darm.reset_tunings()
+
+
+@pytest.mark.parametrize("variant", ["divergent", "melded"])
+@pytest.mark.parametrize("m", [14, 17, 21])
+@pytest.mark.parametrize("desc", [False, True])
+def test_key_value_in_place_merge(swz_kv_tuned, m, variant, desc):
+    """Key-value merges in place (keys and payloads in two swizzled
+    buffers): payload order under heavy ties is the network's, bit for bit."""
+    darm, t = swz_kv_tuned
+    n = 1 << m
+    merges = [L for L in darm.plan_dump(darm.U32, n, True, variant,
+                                        tuning=(t, 4, 4, 8, 2, 3, 1)) if L["kind"] == 2]
+    assert merges and all(L["tma"] == 3 for L in merges)
+    keys = synth.uniform_u32(2100 + m, n) % np.uint32(max(4, n // 64))
+    vals = np.arange(n, dtype=np.uint32)
+    ek, ev = oracle.bitonic_sort(keys, vals, desc=desc)
+    gk, gv = gpu_sort(darm, keys, vals, desc=desc, variant=variant)
+    assert_equal("keys", gk, ek)
+    assert_equal("payload", gv, ev)
+
+
+def test_key_value_in_place_merge_host_buffers(swz_kv_tuned):
+    darm, t = swz_kv_tuned
+    n = 1 << 22
+    keys = synth.uniform_u32(0x5A12, n) % np.uint32(1 << 12)
+    vals = np.arange(n, dtype=np.uint32)
+    ek, ev = oracle.bitonic_sort(keys, vals)
+    hk, hv = keys.copy(), vals.copy()
+    darm.sort_host(hk, hv)
+    assert_equal("keys", hk, ek)
+    assert_equal("payload", hv, ev)

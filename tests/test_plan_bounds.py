@@ -186,3 +186,34 @@ def test_tma_two_window_replay(mutation, monkeypatch):
         return
     with pytest.raises(AssertionError):
         replay()
+
+
+@pytest.mark.parametrize("t", [12, 13])
+@pytest.mark.parametrize("mutation", ["none", "roles", "bit4_no_swap", "bit0_chunks"])
+def test_key_value_swizzled_merge_replay(t, mutation, monkeypatch):
+    """The key-value in-place merge (16 pairs per thread, tiles of 2^12 and
+    2^13 pairs): its word offsets are the 128-byte swizzle of the pair each
+    register holds in every round, the window at bit 4 pair-swapped in
+    lanes 16..31 with the roles of the lowest layer exchanged there; planted
+    mistakes in the offsets or the roles fail the replay."""
+    n = 1 << 17
+    plan = darm.plan_dump(darm.U32, n, True, "melded", tuning=(t, 4, 4, 8, 2, 3, 1))
+    assert any(L["tma"] == 3 for L in plan if L["kind"] == em.MERGE)
+    if mutation == "roles":
+        monkeypatch.setattr(em, "swz_kv_first_is_lower", lambda tid: np.ones_like(tid, dtype=bool))
+    elif mutation in ("bit4_no_swap", "bit0_chunks"):
+        good = em.swz_kv_kernel_word
+
+        def bad(tid, r, a):
+            if mutation == "bit4_no_swap" and a == 4:
+                tl = (tid & 15) | ((tid >> 4) << 8)
+                return ((tl | ((r & 1) << 4)) ^ (((r >> 1) & 7) << 2)) + ((r >> 1) << 5)
+            if mutation == "bit0_chunks" and a == 0:
+                return ((tid >> 1) << 5) + (((((tid & 1) << 2) | (r >> 2)) ^ (tid & 7)) << 2) + (r & 3)
+            return good(tid, r, a)
+        monkeypatch.setattr(em, "swz_kv_kernel_word", bad)
+    if mutation == "none":
+        em.check_plan(plan, n, 4, True, full=True)
+        return
+    with pytest.raises(AssertionError):
+        em.check_plan(plan, n, 4, True, full=True)
