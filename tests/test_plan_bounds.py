@@ -50,13 +50,13 @@ def _tuner_candidates(hv):
 @pytest.mark.parametrize("part", range(4))
 def test_tuner_candidate_plans(hv, part):
     """Tunings the whole-array autotuner tries (and the shuffle-stage tile
-    pass on and off) on an array of 2^16 elements: one candidate in four,
-    the choice rotating through every block of 16 candidates so that each
-    tuning field takes all its values, spread over four cases."""
+    pass on and off) on an array of 2^16 elements: one candidate in 32 per
+    case, the choice rotating through every block of 32 candidates so that
+    over the four cases each tuning field takes all its values."""
     n = 1 << 16
     checked = 0
     for i, tn in enumerate(_tuner_candidates(hv)):
-        if i % 16 != part * 4 + (i // 16) % 4:
+        if i % 32 != part * 8 + (i // 32) % 8:
             continue
         try:
             plan = darm.plan_dump(darm.U32, n, hv, "melded", tuning=tn)
