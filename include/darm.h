@@ -96,6 +96,15 @@ int darm_sort_init(int device, size_t workspace_bytes);
  * graphs, workspace, serving state).  The caller's buffers are untouched. */
 int darm_sort_finalize(void);
 
+/* Diagnostic of the bounded waits: enqueue on `stream` a one-warp kernel
+ * that waits on an mbarrier nothing ever completes, with the same bounded
+ * wait (about one second of %globaltimer) as the passes that stream tiles
+ * with bulk copies.  The wait gives up and latches DARM_ERR_TIMEOUT in the
+ * device status word (darm_device_status reads and clears it); the kernel
+ * then returns, so the context stays usable.  Returns DARM_ERR_NOT_INIT,
+ * DARM_ERR_CUDA (launch failed) or DARM_OK. */
+int darm_check_bounded_wait(void* stream);
+
 /* Human-readable name of a darm_status value (static storage). */
 const char* darm_status_str(int status);
 

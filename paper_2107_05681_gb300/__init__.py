@@ -92,6 +92,7 @@ _sig = {
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u64)], _i32),
     "darm_sort_serve_stop": ([], _i32),
     "darm_sort_serve_inject_fault": ([_i32], _i32),
+    "darm_check_bounded_wait": ([_vp], _i32),
 }
 for _name, (_args, _res) in _sig.items():
     _fn = getattr(lib, _name)
@@ -134,6 +135,13 @@ def device_status() -> int:
     st = ctypes.c_int(0)
     _check(lib.darm_device_status(ctypes.byref(st)), "darm_device_status")
     return st.value
+
+
+def check_bounded_wait(stream=None) -> None:
+    """Enqueue the bounded-wait diagnostic: a kernel waits on an mbarrier
+    that nothing completes, gives up after about a second and latches
+    ERR_TIMEOUT in the device status word (read it with device_status())."""
+    _check(lib.darm_check_bounded_wait(_stream_handle(stream)), "darm_check_bounded_wait")
 
 
 def launch_count() -> int:

@@ -307,6 +307,14 @@ int darm_device_status(int* status) {
   return DARM_OK;
 }
 
+int darm_check_bounded_wait(void* stream) {
+  if (!g_ctx.inited) return DARM_ERR_NOT_INIT;
+  if (launch_bounded_wait_check(g_ctx.d_status, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return DARM_ERR_CUDA;
+  g_ctx.launches.fetch_add(1, std::memory_order_relaxed);
+  return DARM_OK;
+}
+
 int darm_bitonic_sort(uint32_t* keys, uint32_t* vals, size_t n, int dir, int variant,
                       void* stream) {
   return sort_device(KEY_U32, false, keys, vals, n, dir, variant,

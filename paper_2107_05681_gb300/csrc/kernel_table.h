@@ -3,6 +3,8 @@
 // variant).
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 
 namespace darm {
@@ -53,6 +55,9 @@ void for_each_kernel_u32(void (*fn)(const void*, void*), void* ctx);
 void for_each_kernel_u64(void (*fn)(const void*, void*), void* ctx);
 void for_each_tile_kernel_u32(void (*fn)(const void*, void*), void* ctx);
 void for_each_tile_kernel_u64(void (*fn)(const void*, void*), void* ctx);
+// Enqueue the bounded-wait check (tma_u32.cu): one warp waits on an
+// mbarrier nothing completes and latches the timeout status in `status`.
+cudaError_t launch_bounded_wait_check(int* status, cudaStream_t s);
 void for_each_tma_kernel_u32(void (*fn)(const void*, void*), void* ctx);
 void for_each_tile_shfl_kernel_u32(void (*fn)(const void*, void*), void* ctx);
 void for_each_window2_kernel(void (*fn)(const void*, void*), void* ctx);

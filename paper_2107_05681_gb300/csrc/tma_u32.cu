@@ -66,6 +66,29 @@ KernelEntry tma_merge_kernel_u32(bool has_vals, int loge, int logt, int ns, int 
   return KernelEntry{nullptr, 0};
 }
 
+namespace {
+
+// One warp waits on an mbarrier that nothing ever completes, with the bounded
+// wait of the bulk-copy passes: the wait must give up and latch the timeout.
+__global__ void darm_bounded_wait_check_kernel(int* status) {
+  __shared__ __align__(8) unsigned long long bar;
+  const uint32_t b = smem_addr(&bar);
+  if (threadIdx.x == 0) {
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (!mbar_wait_bounded(b, 0u) && threadIdx.x == 0) atomicOr(status, int(kStatusTimeout));
+}
+
+}  // namespace
+
+cudaError_t launch_bounded_wait_check(int* status, cudaStream_t s) {
+  void* args[] = {&status};
+  return cudaLaunchKernel(reinterpret_cast<const void*>(&darm_bounded_wait_check_kernel), dim3(1),
+                          dim3(32), args, 0, s);
+}
+
 void for_each_tma_kernel_u32(void (*fn)(const void*, void*), void* ctx) {
   for (int var = 0; var < 2; ++var)
     for (int ns = 1; ns <= 2; ++ns) {
