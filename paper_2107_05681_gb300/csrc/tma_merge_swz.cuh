@@ -279,8 +279,7 @@ __global__ void __launch_bounds__(1 << (LOGT - 4), (LOGT <= 12) ? 2 : 1)
   using K = uint32_t;
   constexpr int LOGE = 4;
   constexpr int E = 1 << LOGE;
-  using SK = SwzKvSmem<LOGT>;
-  constexpr uint32_t kRows = 1u << (LOGT - 5);  // one box: at most 256 rows
+  using SK = SwzKvSmem<LOGT>;  // a tile's keys (or payloads): one box of 2^(LOGT-5) <= 256 rows
   extern __shared__ __align__(1024) unsigned char swz_smem[];
   const uint32_t sraw = smem_addr(swz_smem);
   const uint32_t sbase = (sraw + 1023u) & ~1023u;
@@ -320,7 +319,6 @@ __global__ void __launch_bounds__(1 << (LOGT - 4), (LOGT <= 12) ? 2 : 1)
     tma_store_2d(&tmv, 0, row, d + SK::kHalf);
     bulk_commit();
   };
-  (void)kRows;
 
   uint32_t tile = blockIdx.x;
   if (tile >= ntiles) return;
