@@ -394,13 +394,15 @@ int darm_autotune_segmented(uint32_t* keys, uint32_t* vals, const uint64_t* seg_
 
 /* Load plans previously written by darm_autotune and
  * darm_autotune_segmented (lines with log2 n = 0 are batch tunings).  A
- * line holds 13 or 14 whitespace-separated fields: key kind (0 32-bit, 1
+ * line holds 13 to 16 whitespace-separated fields: key kind (0 32-bit, 1
  * 64-bit), payload flag, log2 n, log2 tile, log2 elements per thread in
  * tile/merge passes and in window passes, log2 threads of a one-window
  * pass, register windows per window pass, bulk-copy staging buffers of the
  * merge, the form (0 divergent, 1 melded) of tile, window and merge passes,
- * the tuner's time in ms, and optionally 1 for a tile pass with shuffle
- * stages (0 when absent). */
+ * the tuner's time in ms, and optionally the shuffle field (bit 0: tile
+ * pass with shuffle stages, bit 1: merge lane layers by shuffles), log2
+ * elements per thread of merge passes and log2 tile of merge passes (each 0
+ * when absent: the defaults). */
 int darm_load_tune_db(const char* db_path);
 
 /* Forget every tuning loaded or measured so far: later calls plan with the
@@ -426,11 +428,12 @@ int darm_plan_describe(int dtype, size_t n, int has_vals, int variant, char* buf
 
 /* The launch sequence of a whole-array sort as numbers, for checking the
  * planner on the host (no device needed, darm_sort_init not required).
- * tuning (nullable: the tuning a sort of this size would use): 7 int32 -
+ * tuning (nullable: the tuning a sort of this size would use): 8 int32 -
  * log2 tile, log2 elements per thread in tile/merge passes and in window
  * passes, log2 threads of a one-window pass, windows per window pass,
  * bulk-copy staging buffers, shuffle stages (bit 0 tile pass, bit 1 merge
- * passes).  smem_limit: shared
+ * passes), log2 tile of the merge passes (0: the tile pass's; smaller: the
+ * window passes of each stage above the tile also cover the bits between).  smem_limit: shared
  * memory per block the plan may use (0: the device's, or 227 KiB before
  * init).  Writes, per launch, 21 int32 - pass kind (0 tile, 1 window,
  * 2 merge), compile-time tile/merge schedule, bulk-copy buffers (3: the

@@ -563,11 +563,13 @@ _ROUND_FIELDS = ("kind", "p", "a", "cnt", "src", "dst", "lanediv")
 def plan_dump(dtype: int, n: int, has_vals: bool, variant="melded", tuning=None,
               smem_limit: int = 0) -> list[dict]:
     """The launch sequence of a whole-array sort as dicts (host only: no
-    device needed).  tuning: (t, e1, e2, c2, w2, tma, shfl) or None."""
+    device needed).  tuning: (t, e1, e2, c2, w2, tma, shfl[, tm]) or None
+    (tm, the merge passes' log2 tile, 0 when absent: the tile pass's)."""
     import numpy as np
     tn = None
     if tuning is not None:
-        tn = np.ascontiguousarray(np.asarray(tuning, dtype=np.int32))
+        t8 = list(tuning) + [0] * (8 - len(tuning))
+        tn = np.ascontiguousarray(np.asarray(t8[:8], dtype=np.int32))
     cnt = ctypes.c_int(0)
     args = (dtype, n, int(bool(has_vals)), _variant(variant),
             None if tn is None else tn.ctypes.data_as(ctypes.c_void_p), smem_limit)

@@ -46,6 +46,7 @@ Tuning batch_tuning(KeyKind kk, bool has_vals, int cmax) {
   // of up to 2^16 pairs: 4.92 -> 4.52 ms against 4 Ki-pair tiles, when the
   // merge passes ran the table-driven tile kernel).
   if (!tuned && kk == KEY_U32 && has_vals) tn.t = 13;
+  tn.tm = 0;  // batches: merge tiles are the tile pass's
   // tma: staging buffers of the bulk-copy merge, which reads each tile's
   // place from the block table (0: the table-driven tile kernel; no
   // swizzled in-place form for batches)

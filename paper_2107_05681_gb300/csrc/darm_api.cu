@@ -139,7 +139,7 @@ const std::vector<Launch>* cached_plan(KeyKind kk, bool has_vals, int m, int var
                                        uint32_t map_in, uint32_t map_out) {
   const Tuning tn = tuning_for(kk, has_vals, m);
   PlanKey key{int(kk), int(has_vals), m, variant, map_in, map_out, tn.t, tn.e1, tn.e2, tn.c2,
-              tn.w2 * 16 + tn.tma + tn.shfl * 256 + tn.em * 1024,
+              tn.w2 * 16 + tn.tma + tn.shfl * 256 + tn.em * 1024 + tn.tm * 8192,
               tn.var[0] * 4 + tn.var[1] * 2 + tn.var[2]};
   std::lock_guard<std::mutex> lk(g_ctx.mu);
   auto it = g_ctx.plans.find(key);
@@ -566,6 +566,7 @@ int darm_plan_dump(int dtype, size_t n, int has_vals, int variant, const int32_t
     tn.w2 = tuning[4];
     tn.tma = tuning[5];
     tn.shfl = tuning[6];
+    tn.tm = tuning[7];
   }
   if (smem_limit == 0) smem_limit = g_ctx.inited ? g_ctx.smem_limit : size_t(232448 - 64);
   const uint32_t map = dtype == DARM_F32 ? kMapF32 : 0u;

@@ -73,7 +73,13 @@ Tuning default_tuning(KeyKind kk, bool has_vals) {
                  // staging buffers)
     tn.shfl = 1;  // 2^26 float keys: tile pass 0.686 -> 0.639 ms
   } else if (words == 2) {
-    tn.t = 12;  // 4 Ki (key, payload) pairs = 36 KiB with padding: four CTAs per SM
+    // tile pass on 8 Ki pairs, merges on 4 Ki-pair tiles (the window passes
+    // take bit 12): 27 HBM sweeps instead of 29; 2^24 pairs 1.592 ->
+    // 1.539 ms (tile pass 273 -> 307 us, one window and one merge pass
+    // fewer).  For keys alone the 2^15-key tile pass costs about what the
+    // two sweeps save (2.946 -> 2.926 ms), so they keep one tile size.
+    tn.t = 13;
+    tn.tm = 12;
     tn.e1 = 4;
     tn.e2 = 4;
     tn.c2 = 8;
@@ -268,8 +274,14 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
     set_rounds(L.P, rs);
     out.push_back(L);
   }
+  // Merge passes may take smaller tiles than the tile pass (tn.tm < t): the
+  // window passes of every stage p > t then cover layer bits tg .. p-1 and
+  // the merge the bits below tg.  Fewer, longer stages in the tile pass
+  // trade its compute for whole HBM sweeps.
+  const int tg = (tn.tm > 0 && tn.tm < t && tn.tm >= e1) ? tn.tm : t;
+  const size_t merge_smem = size_t(elem_bytes(kk, has_vals)) * smem_words(1u << tg);
   for (int p = t + 1; p <= m; ++p) {
-    // window passes over layer bits t .. p-1, highest bits first.  A pass
+    // window passes over layer bits tg .. p-1, highest bits first.  A pass
     // covers up to w2 * e2 bits: one register window straight from HBM and
     // back, or (w2 = 2) two windows with one exchange through shared memory,
     // whose block holds 32 consecutive elements per window position so that
@@ -277,12 +289,12 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
     // two-window passes hold 2^(c + 2*e2) elements in shared memory (no more
     // than a tile); the c low bits of a block are consecutive elements, at
     // least 8 of them so that every warp access fills whole 32-byte sectors
-    const int c_sm = std::max(3, std::min(5, t - 2 * e2));
-    const bool two = tn.w2 >= 2 && (c_sm + 2 * e2 <= t);
+    const int c_sm = std::max(3, std::min(5, tg - 2 * e2));
+    const bool two = tn.w2 >= 2 && (c_sm + 2 * e2 <= tg);
     const int w_max = two ? 2 * e2 : e2;
     int hi = p - 1;
-    while (hi >= t) {
-      const int nbits = std::min(hi - t + 1, w_max);
+    while (hi >= tg) {
+      const int nbits = std::min(hi - tg + 1, w_max);
       const int lo = hi - nbits + 1;
       const int nr = (nbits + e2 - 1) / e2;
       Launch L{};
@@ -360,26 +372,26 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
       out.push_back(L);
       hi = lo - 1;
     }
-    // merge pass: layers t-1 .. 0 inside each tile
+    // merge pass: layers tg-1 .. 0 inside each tile
     Launch L{};
     L.kind = PASS_MERGE;
     // merge passes may run their own elements per thread (more, smaller
     // threads when the tile needs more resident warps)
     int em = e1;
-    if (tn.em > 0 && tn.em <= 5 && tn.em <= t && (1 << (t - tn.em)) <= 1024 &&
-        merge_round_count(t, tn.em) <= kMaxRounds && has_fixed(kk, has_vals, tn.em, t))
+    if (tn.em > 0 && tn.em <= 5 && tn.em <= tg && (1 << (tg - tn.em)) <= 1024 &&
+        merge_round_count(tg, tn.em) <= kMaxRounds && has_fixed(kk, has_vals, tn.em, tg))
       em = tn.em;
-    L.fixed = has_fixed(kk, has_vals, em, t);
+    L.fixed = has_fixed(kk, has_vals, em, tg);
     L.loge = em;
     L.variant = pick_var(variant, tn, PASS_MERGE);
-    L.grid = uint32_t(1u << (m - t));
-    L.threads = 1u << (t - em);
-    std::vector<Round> rs = merge_rounds(t, em, p);
-    mark_lanes(rs, em, t, t - em);
-    L.smem = uses_smem(rs) ? tile_smem : 0;
-    L.P.b = uint32_t(t);
-    L.P.c = uint32_t(t);
-    L.P.w0 = uint32_t(t);
+    L.grid = uint32_t(1u << (m - tg));
+    L.threads = 1u << (tg - em);
+    std::vector<Round> rs = merge_rounds(tg, em, p);
+    mark_lanes(rs, em, tg, tg - em);
+    L.smem = uses_smem(rs) ? merge_smem : 0;
+    L.P.b = uint32_t(tg);
+    L.P.c = uint32_t(tg);
+    L.P.w0 = uint32_t(tg);
     L.P.s = 0;
     L.P.log2cap = uint32_t(m);
     L.P.map_in = 0;
@@ -390,16 +402,16 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
     size_t tma_smem = 0;
     int tma = tn.tma;
     if (tma == 3 && (g_tensor_maps == 0 ||
-                     tma_merge_kernel_u32(has_vals, em, t, 3, L.variant, &tma_smem).fn == nullptr ||
+                     tma_merge_kernel_u32(has_vals, em, tg, 3, L.variant, &tma_smem).fn == nullptr ||
                      tma_smem > smem_limit))
       tma = 2;  // no swizzled kernel for this shape (or no tensor maps)
     if (kk == KEY_U32 && tma &&
-        tma_merge_kernel_u32(has_vals, em, t, tma, L.variant, &tma_smem).fn != nullptr &&
+        tma_merge_kernel_u32(has_vals, em, tg, tma, L.variant, &tma_smem).fn != nullptr &&
         tma_smem <= smem_limit) {
       L.tma = tma;
       L.smem = tma_smem;
       if ((tn.shfl & 2) != 0 && !has_vals &&
-          tma_merge_shfl_kernel_u32(em, t, tma, L.variant, nullptr).fn != nullptr) {
+          tma_merge_shfl_kernel_u32(em, tg, tma, L.variant, nullptr).fn != nullptr) {
         // two rounds: the top window from the staging buffer, then the lane
         // layers by shuffles and the register layers
         L.mshfl = true;
@@ -407,7 +419,7 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
         Round r0{};
         r0.kind = RK_WINDOW;
         r0.p = uint8_t(p);
-        r0.a = uint8_t(t - em);
+        r0.a = uint8_t(tg - em);
         r0.cnt = uint8_t(em);
         r0.src = LOC_GLOBAL;
         r0.dst = LOC_SMEM;
@@ -415,7 +427,7 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
         r1.kind = RK_WINDOW;
         r1.p = uint8_t(p);
         r1.a = 0;
-        r1.cnt = uint8_t(t - em);  // lane layers t-em-1 .. em, then em register layers
+        r1.cnt = uint8_t(tg - em);  // lane layers tg-em-1 .. em, then em register layers
         r1.src = LOC_SMEM;
         r1.dst = LOC_GLOBAL;
         two.push_back(r0);
@@ -424,7 +436,7 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
       }
       L.P.nblocks = L.grid;
       int per_sm = 1;
-      const void* tfn = tma_merge_kernel_u32(has_vals, em, t, tma, L.variant, nullptr).fn;
+      const void* tfn = tma_merge_kernel_u32(has_vals, em, tg, tma, L.variant, nullptr).fn;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tfn, int(L.threads), L.smem) !=
               cudaSuccess ||
           per_sm < 1) {

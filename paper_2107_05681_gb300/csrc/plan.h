@@ -40,6 +40,8 @@ struct Tuning {
                 // bulk-copy merge passes run their lane layers by shuffles
                 // (two rounds instead of three), where built
   int em = 0;   // log2 elements per thread in merge passes (0: e1)
+  int tm = 0;   // log2 tile of merge passes (0: t); tm < t: the window passes
+                // of every stage above the tile also cover bits tm .. t-1
   int var[3]; // variant per pass kind (used when DARM_AUTO is requested)
 };
 

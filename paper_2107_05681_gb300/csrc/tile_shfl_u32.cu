@@ -29,6 +29,7 @@ int copy_schedule(SRound* out, int cap) {
 }  // namespace
 
 KernelEntry tile_shfl_kernel_u32(bool has_vals, int loge, int logt, int var) {
+  if (!has_vals && loge == 5 && logt == 15) return shfl_entry<false, 5, 15>(var);
   if (!has_vals && loge == 5 && logt == 14) return shfl_entry<false, 5, 14>(var);
   if (!has_vals && loge == 5 && logt == 13) return shfl_entry<false, 5, 13>(var);
   if (!has_vals && loge == 4 && logt == 12) return shfl_entry<false, 4, 12>(var);
@@ -47,9 +48,9 @@ KernelEntry tile_shfl_seg_kernel_u32(bool has_vals, int loge, int logt, int var)
 }
 
 int shfl_schedule_rounds(int logt, int loge, SRound* out, int cap) {
+  if (loge == 5 && logt == 15) return copy_schedule<5, 15>(out, cap);
   if (loge == 5 && logt == 14) return copy_schedule<5, 14>(out, cap);
   if (loge == 5 && logt == 13) return copy_schedule<5, 13>(out, cap);
-  if (loge == 4 && logt == 12) return copy_schedule<4, 12>(out, cap);
   if (loge == 4 && logt == 12) return copy_schedule<4, 12>(out, cap);
   if (loge == 4 && logt == 13) return copy_schedule<4, 13>(out, cap);
   return -1;
@@ -57,6 +58,7 @@ int shfl_schedule_rounds(int logt, int loge, SRound* out, int cap) {
 
 void for_each_tile_shfl_kernel_u32(void (*fn)(const void*, void*), void* ctx) {
   for (int var = 0; var < 2; ++var) {
+    fn(tile_shfl_kernel_u32(false, 5, 15, var).fn, ctx);
     fn(tile_shfl_kernel_u32(false, 5, 14, var).fn, ctx);
     fn(tile_shfl_kernel_u32(false, 5, 13, var).fn, ctx);
     fn(tile_shfl_kernel_u32(false, 4, 12, var).fn, ctx);

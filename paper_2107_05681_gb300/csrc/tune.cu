@@ -104,6 +104,7 @@ int darm_autotune(int dtype, size_t n, int has_vals, const char* db_path) {
           for (int tma = 0; tma <= 3; ++tma) {
             Tuning tn = base;
             tn.tma = tma;
+            tn.tm = 0;  // one tile size here; a smaller merge tile is tried below
             tn.t = t;
             tn.e1 = e1;
             tn.e2 = e2;
@@ -124,6 +125,19 @@ int darm_autotune(int dtype, size_t n, int has_vals, const char* db_path) {
     if (shfl == best.shfl) continue;
     Tuning tn = best;
     tn.shfl = shfl;
+    std::vector<Launch> plan;
+    float kind[3], tot;
+    if (plan_array(plan, kk, hv, m, tn, DARM_AUTO, 0, 0, g_ctx.smem_limit) &&
+        time_plan(plan, kk, keys, vals, kbytes / 4, s, 3, kind, &tot) && tot < best_ms) {
+      best_ms = tot;
+      best = tn;
+    }
+  }
+  // merge passes on tiles half the tile pass's (the window passes take the
+  // bit between): two sweeps fewer for a longer tile pass
+  if (best.t - 1 >= best.e1) {
+    Tuning tn = best;
+    tn.tm = best.t - 1;
     std::vector<Launch> plan;
     float kind[3], tot;
     if (plan_array(plan, kk, hv, m, tn, DARM_AUTO, 0, 0, g_ctx.smem_limit) &&
@@ -155,9 +169,9 @@ int darm_autotune(int dtype, size_t n, int has_vals, const char* db_path) {
   if (db_path) {
     FILE* f = fopen(db_path, "a");
     if (!f) return DARM_ERR_INVALID_ARG;
-    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %.6f %d %d\n", int(kk), int(hv), m, best.t,
+    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %.6f %d %d %d\n", int(kk), int(hv), m, best.t,
             best.e1, best.e2, best.c2, best.w2, best.tma, best.var[0], best.var[1], best.var[2],
-            double(best_ms), best.shfl, best.em);
+            double(best_ms), best.shfl, best.em, best.tm);
     fclose(f);
   }
   return DARM_OK;
@@ -181,15 +195,17 @@ int darm_load_tune_db(const char* db_path) {
   int loaded = 0;
   char line[512];
   std::lock_guard<std::mutex> lk(g_ctx.mu);
-  // one tuning per line: 13 fields, and a 14th (shuffle stages) when present
+  // one tuning per line: 13 fields, then optionally shuffle stages, merge
+  // elements per thread and merge tile
   while (fgets(line, sizeof line, f)) {
     Tuning tn;
-    const int got = sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d %lf %d %d", &kk, &hv, &m,
+    const int got = sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d %lf %d %d %d", &kk, &hv, &m,
                            &tn.t, &tn.e1, &tn.e2, &tn.c2, &tn.w2, &tn.tma, &tn.var[0], &tn.var[1],
-                           &tn.var[2], &ms, &tn.shfl, &tn.em);
+                           &tn.var[2], &ms, &tn.shfl, &tn.em, &tn.tm);
     if (got < 13) continue;
     if (got < 14) tn.shfl = 0;
     if (got < 15) tn.em = 0;
+    if (got < 16) tn.tm = 0;
     if (kk < 0 || kk > 1 || m < 0 || m > 31) continue;
     g_ctx.tuned[std::make_tuple(kk, hv, m)] = tn;  // m == 0: a batch tuning
     ++loaded;

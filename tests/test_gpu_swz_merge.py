@@ -156,3 +156,39 @@ def test_key_value_in_place_merge_host_buffers(swz_kv_tuned):
     darm.sort_host(hk, hv)
     assert_equal("keys", hk, ek)
     assert_equal("payload", hv, ev)
+
+
+@pytest.mark.parametrize("case", [("u32", 15, 14), ("kv", 13, 12), ("kv", 14, 12)])
+@pytest.mark.parametrize("m", [16, 21])
+@pytest.mark.parametrize("desc", [False, True])
+def test_merge_tile_smaller_than_tile(darm, tmp_path, case, m, desc):
+    """Merge passes on tiles smaller than the tile pass's: the window passes
+    of every stage above the tile also take the bits in between (keys with a
+    2^15-key tile pass and 2^14-key merges; pairs with 2^13- or 2^14-pair
+    tile passes and 2^12-pair merges)."""
+    kind, t, tm = case
+    hv = kind == "kv"
+    db = str(tmp_path / "tm.db")
+    with open(db, "w") as f:
+        for mm in range(t + 1, 27):
+            if hv:
+                f.write(f"0 1 {mm} {t} 4 4 8 2 3 1 1 1 0.0 1 0 {tm}\n")
+            else:
+                f.write(f"0 0 {mm} {t} 5 5 8 2 3 1 1 1 0.0 1 0 {tm}\n")
+    darm.reset_tunings()
+    darm.load_tune_db(db)
+    try:
+        n = 1 << m
+        plan = darm.plan_dump(darm.U32, n, hv, "melded",
+                              tuning=(t, 4 if hv else 5, 4 if hv else 5, 8, 2, 3, 1, tm))
+        assert plan[0]["b"] == t and all(L["b"] == tm for L in plan if L["kind"] == 2)
+        keys = synth.uniform_u32(4400 + m + t, n) % np.uint32(max(4, n // 16))
+        vals = np.arange(n, dtype=np.uint32) if hv else None
+        ek, ev = oracle.bitonic_sort(keys, vals, desc=desc)
+        gk, gv = gpu_sort(darm, keys, vals, desc=desc)
+        assert_equal("keys", gk, ek)
+        if hv:
+            assert_equal("payload", gv, ev)
+        assert darm.device_status() == 0
+    finally:
+        darm.reset_tunings()

@@ -36,27 +36,29 @@ def test_full_size_plans_bit_linear(dtype, kb, hv, m):
 
 
 def _tuner_candidates(hv):
-    base_t, base_e1 = (12, 4) if hv else (14, 5)
+    base_t, base_e1 = (13, 4) if hv else (14, 5)
     for t in (base_t - 1, base_t, base_t + 1):
         for e1 in (base_e1 - 1, base_e1):
             for e2 in (3, 4, 5):
                 for w2 in (1, 2):
                     for tma in (0, 1, 2, 3):
                         for shfl in (0, 1, 3):
-                            yield (t, e1, e2, 8, w2, tma, shfl)
+                            for tm in (0, t - 1):
+                                yield (t, e1, e2, 8, w2, tma, shfl, tm)
 
 
 @pytest.mark.parametrize("hv", [False, True])
 @pytest.mark.parametrize("part", range(4))
 def test_tuner_candidate_plans(hv, part):
     """Tunings the whole-array autotuner tries (and the shuffle-stage tile
-    pass on and off) on an array of 2^16 elements: one candidate in 32 per
-    case, the choice rotating through every block of 32 candidates so that
-    over the four cases each tuning field takes all its values."""
+    pass on and off, merges on the tile pass's tile or half of it) on an
+    array of 2^16 elements: one candidate in 64 per case, the choice rotating
+    through every block of 64 candidates so that over the four cases each
+    tuning field takes all its values."""
     n = 1 << 16
     checked = 0
     for i, tn in enumerate(_tuner_candidates(hv)):
-        if i % 32 != part * 8 + (i // 32) % 8:
+        if i % 64 != part * 16 + (i // 64) % 16:
             continue
         try:
             plan = darm.plan_dump(darm.U32, n, hv, "melded", tuning=tn)
