@@ -668,6 +668,9 @@ def run_segmented(args, world, rank, local):
             for kf in ("form_tile", "form_window", "form_merge"):
                 tuned[kf] = "melded" if tuned[kf] == 1 else "divergent"
             tuned["tuner_ms"] = float(f[12])
+            for i, key in ((13, "shuffle"), (14, "e_merge_log2"), (15, "merge_tile_log2")):
+                if len(f) > i:
+                    tuned[key] = int(f[i])
         for _ in range(args.warmup):
             k.copy_(src_k)
             v.copy_(src_v)

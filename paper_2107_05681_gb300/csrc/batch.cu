@@ -46,7 +46,7 @@ Tuning batch_tuning(KeyKind kk, bool has_vals, int cmax) {
   // of up to 2^16 pairs: 4.92 -> 4.52 ms against 4 Ki-pair tiles, when the
   // merge passes ran the table-driven tile kernel).
   if (!tuned && kk == KEY_U32 && has_vals) tn.t = 13;
-  tn.tm = 0;  // batches: merge tiles are the tile pass's
+  if (!tuned) tn.tm = 0;  // one tile size unless a batch tuning asks for a smaller merge tile
   // tma: staging buffers of the bulk-copy merge, which reads each tile's
   // place from the block table (0: the table-driven tile kernel; no
   // swizzled in-place form for batches)
@@ -239,7 +239,8 @@ int batch_append(BatchTables& bt, KeyKind kk, bool has_vals, const Tuning& tn, i
     if (L0.kind == PASS_MERGE && kk == KEY_U32 && (tn.tma == 1 || tn.tma == 2)) {
       // merge blocks are whole tiles of one segment: the persistent
       // bulk-copy merge streams them in, finding each in the table
-      const KernelEntry te = tma_merge_kernel_u32(has_vals, L0.loge, t, tn.tma, L.variant, &tma_smem);
+      const KernelEntry te =
+          tma_merge_kernel_u32(has_vals, L0.loge, int(L0.P.b), tn.tma, L.variant, &tma_smem);
       if (te.fn != nullptr && tma_smem <= g_ctx.smem_limit && int(L.threads) == te.max_threads) {
         int per_sm = 1;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, te.fn, int(L.threads), tma_smem) !=

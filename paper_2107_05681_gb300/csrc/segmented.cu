@@ -339,6 +339,17 @@ extern "C" int darm_autotune_segmented(uint32_t* keys, uint32_t* vals, const uin
           best = tn;
         }
       }
+  // merges on tiles half the tile pass's (the window passes take the bit
+  // between)
+  if (best_ms >= 0.f && best.t - 1 >= best.e1) {
+    Tuning tn = best;
+    tn.tm = best.t - 1;
+    const float ms = time_tuning(tn);
+    if (ms >= 0.f && ms < best_ms) {
+      best_ms = ms;
+      best = tn;
+    }
+  }
   // the divergent or melded form per pass kind (tile, window, merge)
   if (best_ms >= 0.f) {
     const Tuning shape = best;
@@ -366,9 +377,9 @@ extern "C" int darm_autotune_segmented(uint32_t* keys, uint32_t* vals, const uin
   if (db_path) {
     FILE* f = fopen(db_path, "a");
     if (!f) return DARM_ERR_INVALID_ARG;
-    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %.6f\n", int(KEY_U32), int(hv), 0, best.t,
-            best.e1, best.e2, best.c2, best.w2, best.tma, best.var[0], best.var[1], best.var[2],
-            double(best_ms));
+    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %.6f %d %d %d\n", int(KEY_U32), int(hv), 0,
+            best.t, best.e1, best.e2, best.c2, best.w2, best.tma, best.var[0], best.var[1],
+            best.var[2], double(best_ms), best.shfl, best.em, best.tm);
     fclose(f);
   }
   return DARM_OK;
