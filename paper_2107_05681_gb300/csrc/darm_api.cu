@@ -51,21 +51,24 @@ static bool encode_key_rows(CUtensorMap* tm, void* keys, uint64_t rows, uint32_t
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Tensor map of a two-window pass over `nblocks` blocks of 2^14 uint32 keys
-// from `keys`, window bits w0 .. w0+9: dimensions (16 consecutive keys, the
-// 2^(w0-4) positions between them and the windows, bottom window, top
-// window, the blocks above), one box = one block.
-static bool encode_window2_blocks(CUtensorMap* tm, void* keys, uint32_t nblocks, uint32_t w0) {
-  if (g_encode_tiled == nullptr || w0 < 4 || w0 + 12 > 40) return false;
+// Tensor map of a two-window pass over `nblocks` blocks of 16 x 2^(2e)
+// uint32 elements from `base` (keys or payloads), window bits w0 ..
+// w0+2e-1: dimensions (16 consecutive elements, the 2^(w0-4) positions
+// between them and the windows, bottom window, top window, the blocks
+// above), one box = one block.
+static bool encode_window2_blocks(CUtensorMap* tm, void* base, uint32_t nblocks, uint32_t w0,
+                                  int loge) {
+  if (g_encode_tiled == nullptr || w0 < 4 || w0 + 2 * uint32_t(loge) + 2 > 40) return false;
   const uint32_t nmid = w0 - 4;
   if ((uint64_t(nblocks) & ((uint64_t(1) << nmid) - 1)) != 0) return false;
   auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(g_encode_tiled);
-  const cuuint64_t dims[5] = {16, cuuint64_t(1) << nmid, 32, 32, cuuint64_t(nblocks) >> nmid};
-  const cuuint64_t strides[4] = {64, cuuint64_t(4) << w0, cuuint64_t(4) << (w0 + 5),
-                                 cuuint64_t(4) << (w0 + 10)};
-  const cuuint32_t box[5] = {16, 1, 32, 32, 1};
+  const cuuint64_t win = cuuint64_t(1) << loge;
+  const cuuint64_t dims[5] = {16, cuuint64_t(1) << nmid, win, win, cuuint64_t(nblocks) >> nmid};
+  const cuuint64_t strides[4] = {64, cuuint64_t(4) << w0, cuuint64_t(4) << (w0 + loge),
+                                 cuuint64_t(4) << (w0 + 2 * loge)};
+  const cuuint32_t box[5] = {16, 1, cuuint32_t(win), cuuint32_t(win), 1};
   const cuuint32_t elem_strides[5] = {1, 1, 1, 1, 1};
-  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT32, 5, keys, dims, strides, box, elem_strides,
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT32, 5, base, dims, strides, box, elem_strides,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -79,7 +82,7 @@ int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_
     P.vals = vals;
     P.status = g_ctx.d_status;
     const void* fn =
-        L.win2t ? window2_tma_kernel_u32(nullptr).fn
+        L.win2t ? window2_tma_kernel_u32(has_vals, nullptr).fn
         : L.win1 ? window1_kernel(kk == KEY_U64, has_vals, L.loge, int(L.P.c)).fn
         : L.win2 ? ((kk == KEY_U32) ? window2_kernel_u32(has_vals, L.loge, int(L.P.c), L.variant)
                                   : window2_kernel_u64(has_vals, L.loge, int(L.P.c), L.variant)).fn
@@ -92,7 +95,8 @@ int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_
     if (!fn) return DARM_ERR_INVALID_ARG;
     CUtensorMap tmap, tmap2;
     void* args[] = {&P, &tmap, &tmap2};
-    if (L.win2t && !encode_window2_blocks(&tmap, keys, L.P.nblocks, L.P.w0)) {
+    if (L.win2t && (!encode_window2_blocks(&tmap, keys, L.P.nblocks, L.P.w0, L.loge) ||
+                    (has_vals && !encode_window2_blocks(&tmap2, vals, L.P.nblocks, L.P.w0, L.loge)))) {
       fprintf(stderr, "darm: encoding the window pass's tensor map failed\n");
       return DARM_ERR_CUDA;
     }

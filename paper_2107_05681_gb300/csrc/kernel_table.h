@@ -44,10 +44,11 @@ KernelEntry window2_kernel_u32(bool has_vals, int loge, int c, int var);
 // threads, E = 2^loge; nullptr where none was built.
 KernelEntry window1_kernel(bool u64, bool has_vals, int loge, int c);
 KernelEntry window2_kernel_u64(bool has_vals, int loge, int c, int var);
-// The two-window pass of 32-bit keys without payload, 32 keys per thread and
-// 16 consecutive keys per block (window2_tma.cuh): persistent, blocks
-// streamed through three shared-memory buffers by TMA tensor copies.
-KernelEntry window2_tma_kernel_u32(size_t* smem_bytes);
+// The two-window pass of 32-bit keys, 16 consecutive elements per block
+// (window2_tma.cuh): keys alone with 32 per thread, or with a payload with 16
+// pairs per thread; persistent, blocks streamed through three shared-memory
+// buffers by TMA tensor copies.
+KernelEntry window2_tma_kernel_u32(bool has_vals, size_t* smem_bytes);
 
 // Call fn(kernel address, ctx) for every instantiation (used to configure
 // shared-memory limits once per device).

@@ -356,17 +356,26 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
         KernelEntry w2e = (kk == KEY_U32) ? window2_kernel_u32(has_vals, e2, c, L.variant)
                                           : window2_kernel_u64(has_vals, e2, c, L.variant);
         L.win2 = (nr == 2 && w2e.fn != nullptr && int(L.threads) == w2e.max_threads);
-        // keys only, 32 keys per thread, 16 consecutive keys per block: the
-        // TMA-streamed form where tensor maps are available (tma mode 3)
+        // 32-bit keys, 16 consecutive elements per block, 32 keys (or 16
+        // pairs) per thread: the TMA-streamed form where tensor maps are
+        // available (tma mode 3)
         size_t w2t_smem = 0;
-        if (L.win2 && tn.tma == 3 && g_tensor_maps != 0 && kk == KEY_U32 && !has_vals &&
-            e2 == 5 && c == 4 && rs[0].cnt == 5 &&
-            window2_tma_kernel_u32(&w2t_smem).fn != nullptr && w2t_smem <= smem_limit) {
+        const KernelEntry w2t = window2_tma_kernel_u32(has_vals, &w2t_smem);
+        if (L.win2 && tn.tma == 3 && g_tensor_maps != 0 && kk == KEY_U32 &&
+            e2 == (has_vals ? 4 : 5) && c == 4 && rs[0].cnt == e2 && w2t.fn != nullptr &&
+            int(L.threads) == w2t.max_threads && w2t_smem <= smem_limit) {
+          int per_sm = 1;
+          if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, w2t.fn, int(L.threads), w2t_smem) !=
+                  cudaSuccess ||
+              per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+          }
           L.win2 = false;
           L.win2t = true;
           L.smem = w2t_smem;
           L.P.nblocks = L.grid;
-          L.grid = std::min<uint32_t>(L.grid, uint32_t(std::max(1, g_sms_for_plans)));
+          L.grid = std::min<uint32_t>(L.grid, uint32_t(std::max(1, g_sms_for_plans) * per_sm));
         }
       }
       out.push_back(L);

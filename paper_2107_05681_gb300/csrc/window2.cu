@@ -49,13 +49,18 @@ KernelEntry window2_kernel_u64(bool has_vals, int loge, int c, int var) {
   return KernelEntry{nullptr, 0};
 }
 
-KernelEntry window2_tma_kernel_u32(size_t* smem_bytes) {
-  if (smem_bytes) *smem_bytes = W2tSmem::kBytes;
-  return KernelEntry{reinterpret_cast<const void*>(&darm_window2_tma_kernel), kW2tThreads};
+KernelEntry window2_tma_kernel_u32(bool has_vals, size_t* smem_bytes) {
+  if (has_vals) {
+    if (smem_bytes) *smem_bytes = W2t<true>::kBytes;
+    return KernelEntry{reinterpret_cast<const void*>(&darm_window2_tma_kernel<true>), W2t<true>::kThreads};
+  }
+  if (smem_bytes) *smem_bytes = W2t<false>::kBytes;
+  return KernelEntry{reinterpret_cast<const void*>(&darm_window2_tma_kernel<false>), W2t<false>::kThreads};
 }
 
 void for_each_window2_kernel(void (*fn)(const void*, void*), void* ctx) {
-  fn(window2_tma_kernel_u32(nullptr).fn, ctx);
+  fn(window2_tma_kernel_u32(false, nullptr).fn, ctx);
+  fn(window2_tma_kernel_u32(true, nullptr).fn, ctx);
   for (int var = 0; var < 2; ++var) {
     fn(window2_kernel_u32(true, 4, 4, var).fn, ctx);
     fn(window2_kernel_u32(true, 4, 5, var).fn, ctx);

@@ -1,27 +1,30 @@
-// window2_tma.cuh - two-window pass of 32-bit keys (no payload) that streams
-// its blocks through shared memory with TMA tensor copies and works on them
-// in place.
+// window2_tma.cuh - two-window pass of 32-bit keys (alone, or with a 32-bit
+// payload) that streams its blocks through shared memory with TMA tensor
+// copies and works on them in place.
 //
-// A two-window pass runs up to ten layers j >= T of one stage k (layer bits
-// w0 .. w0+9) on blocks of 2^14 keys: 16 consecutive keys (local bits
-// 0..3) at each of the 1024 positions of the two windows (local bits 4..8:
-// layer bits w0..w0+4, local bits 9..13: layer bits w0+5..w0+9).  The plain
+// A two-window pass runs up to 2e layers j >= T of one stage k (layer bits
+// w0 .. w0+2e-1) on blocks of 16 x 2^(2e) elements: 16 consecutive elements
+// (local bits 0..3) at each position of the two windows (local bits
+// 4..3+e: layer bits w0..w0+e-1, local bits 4+e..3+2e: the top window).
+// Keys alone: e = 5, 32 keys per thread, 512 threads; with a payload: e = 4,
+// 16 pairs per thread, 256 threads, keys and payloads in two halves of each
+// block buffer (two tensor maps, same box).  The plain
 // two-window kernel (window2_kernel.cuh) loads each thread's 32 keys
 // straight from HBM into registers, exchanges them once through shared
 // memory and stores them from registers; at two CTAs per SM it stalls on
 // those loads and stores (about 94 us per pass on 2^26 keys against 75 us
 // for a one-window pass).  Here, as in the in-place merge
 // (tma_merge_swz.cuh):
-//   - a 5-D tensor map views the array as (16 consecutive keys, the bits
-//     between them and the windows, bottom window, top window, the bits
-//     above), so one box of 16 x 1 x 32 x 32 x 1 keys is one block, dense in
+//   - a 5-D tensor map views the array as (16 consecutive elements, the
+//     bits between them and the windows, bottom window, top window, the bits
+//     above), so one box of 16 x 1 x 2^e x 2^e x 1 is one block, dense in
 //     shared memory in local-index order (no swizzle);
 //   - persistent CTAs keep three block buffers: blocks stream in two ahead,
 //     both rounds read and write the thread's own 32 keys in place, and one
 //     thread hands the finished block to a bulk tensor store;
 //   - round 0 (registers on the top window) puts 32 consecutive words on a
 //     warp's lanes.  In round 1 (registers on the bottom window) a warp's two
-//     half-warps sit 512 words apart, on the same 16 banks; so lanes 16..31
+//     half-warps sit 2^(4+e) words apart, on the same 16 banks; so lanes 16..31
 //     hold their registers in pair-swapped order (register r holds bottom
 //     window position r ^ 1), which moves them to the other 16 banks.  That
 //     swap reverses which register of a pair holds the lower index only in
@@ -36,12 +39,15 @@
 
 namespace darm {
 
-constexpr int kW2tLog2Block = 14;  // 16 consecutive keys x 2 windows of 5 bits
-constexpr int kW2tThreads = 512;
-
-struct W2tSmem {
-  static constexpr uint32_t kBlockBytes = 4u << kW2tLog2Block;
-  static constexpr size_t kBytes = 1024 + size_t(kSwzBuffers) * kBlockBytes + 8 * kSwzBuffers;
+// Block shape of the TMA two-window pass: V = with a payload.
+template <bool V>
+struct W2t {
+  static constexpr int kLogE = V ? 4 : 5;                  // window bits e
+  static constexpr int kLog2Block = 4 + 2 * kLogE;         // 16 consecutive x 2 windows
+  static constexpr int kThreads = 1 << (kLog2Block - kLogE);
+  static constexpr uint32_t kHalf = 4u << kLog2Block;      // keys (or payloads) of a block
+  static constexpr uint32_t kSet = V ? 2 * kHalf : kHalf;  // one block buffer
+  static constexpr size_t kBytes = 1024 + size_t(kSwzBuffers) * kSet + 8 * kSwzBuffers;
 };
 
 __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* tm, int c1, int c4,
@@ -61,19 +67,23 @@ __device__ __forceinline__ void tma_store_5d(const CUtensorMap* tm, int c1, int 
 }
 
 // One two-window pass over P.nblocks blocks (block b: mid bits b mod 2^(w0-4)
-// between the consecutive keys and the windows, high bits b >> (w0-4)).
-// Round 0 runs the top window's five layers, round 1 the top
-// P.rounds[1].cnt layers of the bottom window.
-__global__ void __launch_bounds__(kW2tThreads, 1)
-    darm_window2_tma_kernel(const __grid_constant__ PassParams P, const __grid_constant__ CUtensorMap tmap) {
+// between the consecutive elements and the windows, high bits b >> (w0-4)).
+// Round 0 runs the top window's e layers, round 1 the top P.rounds[1].cnt
+// layers of the bottom window.  `tmv` maps the payload (V only).
+template <bool V>
+__global__ void __launch_bounds__(W2t<V>::kThreads, V ? 2 : 1)
+    darm_window2_tma_kernel(const __grid_constant__ PassParams P, const __grid_constant__ CUtensorMap tmk,
+                            const __grid_constant__ CUtensorMap tmv) {
   using K = uint32_t;
-  constexpr int E = 32;
-  constexpr uint32_t kBlockB = W2tSmem::kBlockBytes;
+  using S = W2t<V>;
+  constexpr int LOGE = S::kLogE;
+  constexpr int E = 1 << LOGE;
+  constexpr int A0 = 4 + LOGE;  // round 0 window bits A0 .. A0+e-1
   extern __shared__ __align__(1024) unsigned char w2t_smem[];
   const uint32_t sraw = smem_addr(w2t_smem);
   const uint32_t sbase = (sraw + 1023u) & ~1023u;
   unsigned char* sbuf = w2t_smem + (sbase - sraw);
-  const uint32_t bar0 = sbase + uint32_t(kSwzBuffers) * kBlockB;
+  const uint32_t bar0 = sbase + uint32_t(kSwzBuffers) * S::kSet;
   const uint32_t tid = threadIdx.x;
   const uint32_t nblocks = P.nblocks;
   const uint32_t w0 = P.w0;
@@ -82,22 +92,26 @@ __global__ void __launch_bounds__(kW2tThreads, 1)
   const uint32_t capmask = (1u << P.log2cap) - 1u;
   const uint32_t p = P.rounds[0].p;
   const int cnt1 = P.rounds[1].cnt;
-  const CUtensorMap* tm = &tmap;
 
   auto issue_load = [&](uint32_t blk, int b) {  // thread 0
     const uint32_t bar = bar0 + 8u * uint32_t(b);
-    mbar_expect_tx(bar, kBlockB);
-    tma_load_5d(sbase + uint32_t(b) * kBlockB, tm, int(blk & midmask), int(blk >> nmid), bar);
+    const uint32_t d = sbase + uint32_t(b) * S::kSet;
+    mbar_expect_tx(bar, S::kSet);
+    tma_load_5d(d, &tmk, int(blk & midmask), int(blk >> nmid), bar);
+    if (V) tma_load_5d(d + S::kHalf, &tmv, int(blk & midmask), int(blk >> nmid), bar);
   };
   auto issue_store = [&](uint32_t blk, int b) {  // thread 0
-    tma_store_5d(tm, int(blk & midmask), int(blk >> nmid), sbase + uint32_t(b) * kBlockB);
+    const uint32_t d = sbase + uint32_t(b) * S::kSet;
+    tma_store_5d(&tmk, int(blk & midmask), int(blk >> nmid), d);
+    if (V) tma_store_5d(&tmv, int(blk & midmask), int(blk >> nmid), d + S::kHalf);
     bulk_commit();
   };
 
   uint32_t blk = blockIdx.x;
   if (blk >= nblocks) return;
   if (tid == 0) {
-    asm volatile("prefetch.tensormap [%0];" ::"l"(tm) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmk) : "memory");
+    if (V) asm volatile("prefetch.tensormap [%0];" ::"l"(&tmv) : "memory");
 #pragma unroll
     for (int b = 0; b < kSwzBuffers; ++b) mbar_init(bar0 + 8u * uint32_t(b), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -113,15 +127,15 @@ __global__ void __launch_bounds__(kW2tThreads, 1)
     }
   }
 
-  // round 1: lanes on local bits 0..3 and 9..13; lanes 16..31 of a warp hold
+  // round 1: lanes on local bits 0..3 and A0..; lanes 16..31 of a warp hold
   // bottom-window position r ^ 1 in register r
   const uint32_t tw0 = (tid >> 4) & 1u;
-  const uint32_t base1 = (tid & 15u) | ((tid >> 4) << 9);
+  const uint32_t base1 = (tid & 15u) | ((tid >> 4) << A0);
   const uint32_t even1 = base1 + (tw0 << 4);  // register r even: base1 + ((r + tw0) << 4)
   const uint32_t odd1 = base1 - (tw0 << 4);   // register r odd:  base1 + ((r - tw0) << 4)
 
   K kr[E];
-  uint32_t vr[E];  // unused (no payload); window_side's signature
+  uint32_t vr[E];
 #pragma unroll
   for (int r = 0; r < E; ++r) vr[r] = 0;
 
@@ -140,19 +154,26 @@ __global__ void __launch_bounds__(kW2tThreads, 1)
     }
     phase ^= 1u << b;
     pending &= ~(1u << b);
-    K* sk = reinterpret_cast<K*>(sbuf + size_t(b) * kBlockB);
-    const uint32_t gblk = ((blk & midmask) << 4) | ((blk >> nmid) << (w0 + 10u));
+    K* sk = reinterpret_cast<K*>(sbuf + size_t(b) * S::kSet);
+    uint32_t* sv = reinterpret_cast<uint32_t*>(sbuf + size_t(b) * S::kSet + S::kHalf);
+    const uint32_t gblk = ((blk & midmask) << 4) | ((blk >> nmid) << (w0 + 2u * LOGE));
     const bool asc = (((gblk | P.dir_base) & (1u << p) & capmask) == 0u);
 
-    // round 0: the top window's five layers
+    // round 0: the top window's e layers
 #pragma unroll
-    for (int r = 0; r < E; ++r) kr[r] = sk[tid + (uint32_t(r) << 9)];
+    for (int r = 0; r < E; ++r) {
+      kr[r] = sk[tid + (uint32_t(r) << A0)];
+      if (V) vr[r] = sv[tid + (uint32_t(r) << A0)];
+    }
     if (asc)
-      window_side<K, false, 5, true, true>(kr, vr, 5);
+      window_side<K, V, LOGE, true, !V>(kr, vr, LOGE);
     else
-      window_side<K, false, 5, false, true>(kr, vr, 5);
+      window_side<K, V, LOGE, false, !V>(kr, vr, LOGE);
 #pragma unroll
-    for (int r = 0; r < E; ++r) sk[tid + (uint32_t(r) << 9)] = kr[r];
+    for (int r = 0; r < E; ++r) {
+      sk[tid + (uint32_t(r) << A0)] = kr[r];
+      if (V) sv[tid + (uint32_t(r) << A0)] = vr[r];
+    }
     __syncthreads();
     {
       const uint32_t nb = blk + uint32_t(kSwzBuffers - 1) * gridDim.x;
@@ -168,29 +189,46 @@ __global__ void __launch_bounds__(kW2tThreads, 1)
     }
     // round 1: the bottom window's top cnt1 layers
 #pragma unroll
-    for (int r = 0; r < E; ++r) kr[r] = sk[((r & 1) ? odd1 : even1) + (uint32_t(r) << 4)];
-    if (asc)
-      window_side<K, false, 5, true, true>(kr, vr, cnt1 < 4 ? cnt1 : 4);
-    else
-      window_side<K, false, 5, false, true>(kr, vr, cnt1 < 4 ? cnt1 : 4);
-    if (cnt1 == 5) {
-      // layer of the window's lowest bit: pair (r, r + 1); in lanes 16..31
-      // register r + 1 holds the lower index
-      const bool keep_lo_first = asc != (tw0 != 0u);
-#pragma unroll
-      for (int r = 0; r < E; r += 2) {
-        const K lo = kmin(kr[r], kr[r + 1]);
-        const K hi = kmax(kr[r], kr[r + 1]);
-        kr[r] = keep_lo_first ? lo : hi;
-        kr[r + 1] = keep_lo_first ? hi : lo;
-      }
+    for (int r = 0; r < E; ++r) {
+      const uint32_t w = ((r & 1) ? odd1 : even1) + (uint32_t(r) << 4);
+      kr[r] = sk[w];
+      if (V) vr[r] = sv[w];
     }
+    auto round1 = [&](auto asc_c) {
+      constexpr bool ASC = decltype(asc_c)::value;
+      window_side<K, V, LOGE, ASC, !V>(kr, vr, cnt1 < LOGE - 1 ? cnt1 : LOGE - 1);
+      if (cnt1 == LOGE) {
+        // layer of the window's lowest bit: pair (r, r + 1); in lanes
+        // 16..31 register r + 1 holds the lower index
+        const bool flip = tw0 != 0u;
+#pragma unroll
+        for (int r = 0; r < E; r += 2) {
+          if constexpr (V) {
+            ce_kv_flip<ASC>(kr[r], kr[r + 1], vr[r], vr[r + 1], flip);
+          } else {
+            const bool keep_lo_first = ASC != flip;
+            const K lo = kmin(kr[r], kr[r + 1]);
+            const K hi = kmax(kr[r], kr[r + 1]);
+            kr[r] = keep_lo_first ? lo : hi;
+            kr[r + 1] = keep_lo_first ? hi : lo;
+          }
+        }
+      }
+    };
+    if (asc)
+      round1(std::true_type{});
+    else
+      round1(std::false_type{});
     if (P.map_out != 0u) {
 #pragma unroll
       for (int r = 0; r < E; ++r) kr[r] = key_out<K>(kr[r], P.map_out);
     }
 #pragma unroll
-    for (int r = 0; r < E; ++r) sk[((r & 1) ? odd1 : even1) + (uint32_t(r) << 4)] = kr[r];
+    for (int r = 0; r < E; ++r) {
+      const uint32_t w = ((r & 1) ? odd1 : even1) + (uint32_t(r) << 4);
+      sk[w] = kr[r];
+      if (V) sv[w] = vr[r];
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) issue_store(blk, b);

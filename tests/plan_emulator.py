@@ -60,16 +60,17 @@ def swz_kernel_word(tid, r, rd, logt):
 
 
 def tma_box_global(L, blk, l):
-    """Global index of element l of block blk of a TMA two-window pass: the
-    tensor map's coordinates (16 consecutive keys, the w0 - 4 bits between
-    them and the windows, bottom window, top window, the bits above) with
-    the strides the host encodes (1, 16, 2^w0, 2^(w0+5), 2^(w0+10) keys)."""
-    w0 = L["w0"]
+    """Global index of element l of block blk of a TMA two-window pass with
+    windows of e bits: the tensor map's coordinates (16 consecutive
+    elements, the w0 - 4 bits between them and the windows, bottom window,
+    top window, the bits above) with the strides the host encodes (1, 16,
+    2^w0, 2^(w0+e), 2^(w0+2e) elements)."""
+    w0, e = L["w0"], L["loge"]
     nmid = w0 - 4
     mid = blk & ((1 << nmid) - 1)
     high = blk >> nmid
-    d0, bw, tw = l & 15, (l >> 4) & 31, l >> 9
-    return d0 + 16 * mid + (bw << w0) + (tw << (w0 + 5)) + (high << (w0 + 10))
+    d0, bw, tw = l & 15, (l >> 4) & ((1 << e) - 1), l >> (4 + e)
+    return d0 + 16 * mid + (bw << w0) + (tw << (w0 + e)) + (high << (w0 + 2 * e))
 
 
 def w2t_keeps_min_first(tid):

@@ -142,18 +142,20 @@ def test_swizzled_merge_replay(t, mutation, monkeypatch):
         em.check_plan(plan, n, 4, False, full=True)
 
 
+@pytest.mark.parametrize("hv", [False, True])
 @pytest.mark.parametrize("mutation", ["none", "roles", "box_stride", "no_swap_in_kernel"])
-def test_tma_two_window_replay(mutation, monkeypatch):
-    """The TMA two-window pass (keys only): the ten-layer two-window launch
-    of the 2^24-key plan (the one that runs the pair-swapped lowest layer)
+def test_tma_two_window_replay(mutation, hv, monkeypatch):
+    """The TMA two-window pass (keys alone, or pairs): the two-window launch
+    of the 2^24-element plan with both windows full (the one that runs the
+    pair-swapped lowest layer)
     replayed in full on eight of its blocks, the whole plan on single bits
     and samples.  The tensor box's geometry must give every
     element's global index, and the pair-swapped register order of round 1
     must keep the minimum on the register that holds the lower index;
     planted mistakes in either fail the replay."""
     n = 1 << 24
-    plan = darm.plan_dump(darm.U32, n, False, "melded")
-    w2t = [L for L in plan if L["win2"] == 2 and L["rounds"][1]["cnt"] == 5]
+    plan = darm.plan_dump(darm.U32, n, hv, "melded")
+    w2t = [L for L in plan if L["win2"] == 2 and L["rounds"][1]["cnt"] == L["loge"]]
     assert w2t, "no ten-layer TMA two-window pass"
     w2t = w2t[:1]
     if mutation == "roles":
@@ -162,7 +164,8 @@ def test_tma_two_window_replay(mutation, monkeypatch):
         good = em.tma_box_global
 
         def bad(L, blk, l):
-            return good(L, blk, l) + ((l >> 9) & 1) * (1 << L["w0"])  # top-window stride off by 2^w0
+            # top-window stride off by 2^w0
+            return good(L, blk, l) + ((l >> (4 + L["loge"])) & 1) * (1 << L["w0"])
         monkeypatch.setattr(em, "tma_box_global", bad)
     elif mutation == "no_swap_in_kernel":
         # the kernel's register order without the swap, the roles unchanged
@@ -177,14 +180,14 @@ def test_tma_two_window_replay(mutation, monkeypatch):
             seq = []
             nb = L["nblocks"]
             some = sorted({0, 1, nb - 1} | set(np.random.default_rng(7).integers(0, nb, 5).tolist()))
-            em.check_launch_full(em.Kernel(L, 4, False), n, seq, blocks=some)
+            em.check_launch_full(em.Kernel(L, 4, hv), n, seq, blocks=some)
             p = L["rounds"][0]["p"]
-            top = L["w0"] + 9
+            top = L["w0"] + 2 * L["loge"] - 1
             assert seq == [(p, q) for q in range(top, top - len(seq), -1)], seq
 
     if mutation == "none":
         replay()
-        em.check_plan(plan, n, 4, False, full=False, rng=np.random.default_rng(24))
+        em.check_plan(plan, n, 4, hv, full=False, rng=np.random.default_rng(24))
         return
     with pytest.raises(AssertionError):
         replay()
