@@ -248,6 +248,10 @@ int darm_sort_init(int device, size_t workspace_bytes) {
     return DARM_ERR_CUDA;
   for (cudaEvent_t& e : g_ctx.host_chunk_ev)
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return DARM_ERR_CUDA;
+  if (cudaStreamCreateWithFlags(&g_ctx.host_stream2, cudaStreamNonBlocking) != cudaSuccess)
+    return DARM_ERR_CUDA;
+  if (cudaEventCreateWithFlags(&g_ctx.host_join_ev, cudaEventDisableTiming) != cudaSuccess)
+    return DARM_ERR_CUDA;
   if (workspace_bytes) {
     if (cudaMalloc(&g_ctx.ws, workspace_bytes) != cudaSuccess) return DARM_ERR_OOM;
     g_ctx.ws_bytes = workspace_bytes;
@@ -268,6 +272,10 @@ int darm_sort_finalize(void) {
   if (g_ctx.d_status) cudaFree(g_ctx.d_status);
   if (g_ctx.host_stream) cudaStreamDestroy(g_ctx.host_stream);
   if (g_ctx.host_copy_stream) cudaStreamDestroy(g_ctx.host_copy_stream);
+  if (g_ctx.host_stream2) cudaStreamDestroy(g_ctx.host_stream2);
+  if (g_ctx.host_join_ev) cudaEventDestroy(g_ctx.host_join_ev);
+  g_ctx.host_stream2 = nullptr;
+  g_ctx.host_join_ev = nullptr;
   for (cudaEvent_t& e : g_ctx.host_chunk_ev) {
     if (e) cudaEventDestroy(e);
     e = nullptr;
@@ -349,7 +357,8 @@ namespace {
 //     each chunk runs as soon as it has arrived;
 //   - once the first half (4 chunks) has arrived and been tiled, stages
 //     2^(t+1) .. 2^(m-1) run on that half while the second half is still
-//     being copied; then the second half's tile passes and stages;
+//     being copied; the second half's tile passes run on a second stream as
+//     its chunks arrive, beside those stages; then the second half's stages;
 //   - the final stage runs over the whole array; its trailing passes whose
 //     blocks lie inside one chunk (the merge, and window passes below bit
 //     m-3) run chunk by chunk, and each chunk is copied back while the next
@@ -429,14 +438,22 @@ int sort_host_chunked(KeyKind kk, bool f32, void* keys_out, uint32_t* vals_out, 
     if (cudaEventRecord(g_ctx.host_chunk_ev[c], cps) != cudaSuccess) return DARM_ERR_CUDA;
   }
   int rc;
+  // Tile passes as the chunks arrive: the first half's on `s`, the second
+  // half's on a second stream, so that they run while `s` works through the
+  // first half's stages (the tile passes are bound by the ALU, those stages
+  // by HBM); `s` joins them before the second half's stages.
+  cudaStream_t s2 = g_ctx.host_stream2;
+  for (int c = 0; c < kHostChunks; ++c) {
+    cudaStream_t ts = (c < kHostChunks / 2) ? s : s2;
+    const size_t off = size_t(c) * cn;
+    if (cudaStreamWaitEvent(ts, g_ctx.host_chunk_ev[c], 0) != cudaSuccess) return DARM_ERR_CUDA;
+    tile[0].P.dir_base = uint32_t(off);
+    rc = launch_plan(tile, kk, static_cast<char*>(dk) + off * ksz, hv ? dv + off : nullptr, ts);
+    if (rc != DARM_OK) return rc;
+  }
+  if (cudaEventRecord(g_ctx.host_join_ev, s2) != cudaSuccess) return DARM_ERR_CUDA;
   for (int h = 0; h < 2; ++h) {
-    for (int c = h * kHostChunks / 2; c < (h + 1) * kHostChunks / 2; ++c) {
-      const size_t off = size_t(c) * cn;
-      if (cudaStreamWaitEvent(s, g_ctx.host_chunk_ev[c], 0) != cudaSuccess) return DARM_ERR_CUDA;
-      tile[0].P.dir_base = uint32_t(off);
-      rc = launch_plan(tile, kk, static_cast<char*>(dk) + off * ksz, hv ? dv + off : nullptr, s);
-      if (rc != DARM_OK) return rc;
-    }
+    if (h == 1 && cudaStreamWaitEvent(s, g_ctx.host_join_ev, 0) != cudaSuccess) return DARM_ERR_CUDA;
     const size_t off = size_t(h) * hn;
     for (Launch& L : half) L.P.dir_base = uint32_t(off);
     rc = launch_plan(half, kk, static_cast<char*>(dk) + off * ksz, hv ? dv + off : nullptr, s);
@@ -502,6 +519,7 @@ int darm_bitonic_sort_host(void* keys, uint32_t* vals, size_t n, int dtype, int 
       // copies already enqueued must not outlive the call: the workspace and
       // the caller's buffers are reused once it returns
       cudaStreamSynchronize(g_ctx.host_copy_stream);
+      cudaStreamSynchronize(g_ctx.host_stream2);
       cudaStreamSynchronize(s);
       return rc;
     }

@@ -26,6 +26,8 @@ struct Context {
   int* d_status = nullptr;           // device status word
   cudaStream_t host_stream = nullptr;  // stream of host-buffer sorts
   cudaStream_t host_copy_stream = nullptr;  // their chunked host->device copies
+  cudaStream_t host_stream2 = nullptr;      // tile passes of the second half
+  cudaEvent_t host_join_ev = nullptr;       // ... joined back into host_stream
   cudaEvent_t host_chunk_ev[8] = {};        // one per chunk copied
   void* ws = nullptr;                // workspace of host-buffer sorts
   size_t ws_bytes = 0;
