@@ -437,7 +437,8 @@ int darm_plan_describe(int dtype, size_t n, int has_vals, int variant, char* buf
  * memory per block the plan may use (0: the device's, or 227 KiB before
  * init).  Writes, per launch, 21 int32 - pass kind (0 tile, 1 window,
  * 2 merge), compile-time tile/merge schedule, bulk-copy buffers (3: the
- * merge in place in swizzled buffers), one-window and two-window
+ * merge in place in swizzled buffers; 4: the same with two buffers per
+ * CTA), one-window and two-window
  * compile-time shapes (two-window 2: streamed by TMA), shuffle stages,
  * log2 elements per
  * thread, form, grid, threads, shared memory bytes, then the block bit map

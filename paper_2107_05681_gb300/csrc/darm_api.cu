@@ -100,7 +100,7 @@ int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_
       fprintf(stderr, "darm: encoding the window pass's tensor map failed\n");
       return DARM_ERR_CUDA;
     }
-    if (L.tma == 3) {
+    if (L.tma >= 3) {
       // the tiles this launch covers, as rows of 32 keys (and payloads)
       const int rows_log2 = int(L.P.b) - 5;
       const uint64_t rows = uint64_t(L.P.nblocks) << rows_log2;

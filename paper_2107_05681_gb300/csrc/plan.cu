@@ -84,9 +84,10 @@ Tuning default_tuning(KeyKind kk, bool has_vals) {
     tn.e2 = 4;
     tn.c2 = 8;
     tn.w2 = 2;
-    tn.tma = 3;   // in place, keys and payloads in swizzled buffers: 2^24
-                  // pairs, merge pass 55.0 -> 51.0 us (else 1: one staging
-                  // buffer)
+    tn.tma = 4;   // in place, keys and payloads in swizzled buffers, two
+                  // per CTA and three CTAs per SM: 2^24 pairs, merge pass
+                  // 55.0 -> 51.0 us with three buffers (two CTAs per SM),
+                  // 50.3 -> 49.3 us with two (sort 1.505 -> 1.486 ms)
     tn.shfl = 1;  // 2^24 key-value pairs: tile pass 0.335 -> 0.267 ms
   } else {
     tn.t = 12;  // 4 Ki elements of 12 bytes = 48 KiB
@@ -361,7 +362,7 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
         // available (tma mode 3)
         size_t w2t_smem = 0;
         const KernelEntry w2t = window2_tma_kernel_u32(has_vals, &w2t_smem);
-        if (L.win2 && tn.tma == 3 && g_tensor_maps != 0 && kk == KEY_U32 &&
+        if (L.win2 && tn.tma >= 3 && g_tensor_maps != 0 && kk == KEY_U32 &&
             e2 == (has_vals ? 4 : 5) && c == 4 && rs[0].cnt == e2 && w2t.fn != nullptr &&
             int(L.threads) == w2t.max_threads && w2t_smem <= smem_limit) {
           int per_sm = 1;
@@ -410,6 +411,10 @@ bool plan_array(std::vector<Launch>& out, KeyKind kk, bool has_vals, int m, cons
     // bulk copies while the current one is processed (one CTA per SM)
     size_t tma_smem = 0;
     int tma = tn.tma;
+    if (tma == 4 && (g_tensor_maps == 0 ||
+                     tma_merge_kernel_u32(has_vals, em, tg, 4, L.variant, &tma_smem).fn == nullptr ||
+                     tma_smem > smem_limit))
+      tma = 3;  // no two-buffer in-place kernel for this shape
     if (tma == 3 && (g_tensor_maps == 0 ||
                      tma_merge_kernel_u32(has_vals, em, tg, 3, L.variant, &tma_smem).fn == nullptr ||
                      tma_smem > smem_limit))
@@ -463,7 +468,7 @@ std::string describe(const std::vector<Launch>& plan) {
   std::ostringstream os;
   static const char* names[] = {"tile", "window", "merge"};
   for (const Launch& L : plan) {
-    os << names[L.kind] << (L.fixed ? "*" : "") << (L.shfl ? "~" : "") << (L.win2t || L.tma == 3 ? "^" : "") << " E=" << (1 << L.loge) << " var=" << L.variant << " grid=" << L.grid
+    os << names[L.kind] << (L.fixed ? "*" : "") << (L.shfl ? "~" : "") << (L.win2t || L.tma >= 3 ? "^" : "") << " E=" << (1 << L.loge) << " var=" << L.variant << " grid=" << L.grid
        << " threads=" << L.threads << " smem=" << L.smem << " b=" << L.P.b << " c=" << L.P.c
        << " w0=" << L.P.w0 << " rounds=" << L.P.nrounds << "\n";
   }

@@ -61,7 +61,9 @@ struct Launch {
   int tma;     // persistent merge with bulk-copy prefetch into this many
                // staging buffers (tma_merge.cuh); 3: in place in three
                // swizzled tile buffers with bulk tensor stores
-               // (tma_merge_swz.cuh); 0: plain merge kernel
+               // (tma_merge_swz.cuh); 4: the same with two buffers per CTA
+               // (key-value tiles of 2^12 pairs: three CTAs per SM); 0:
+               // plain merge kernel
   bool win2;   // two-window pass with a compile-time shape (window2_kernel.cuh)
   bool win1;   // one-window pass with a compile-time shape (window1_kernel.cuh)
   bool win2t;  // two-window pass streamed through shared memory by TMA

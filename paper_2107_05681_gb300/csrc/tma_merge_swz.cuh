@@ -254,11 +254,11 @@ __global__ void __launch_bounds__(1 << (LOGT - 5), (LOGT <= 13) ? 2 : 1)
 // The compare-exchange is Fig. 1's strict swap of (key, payload) by key.
 namespace darm {
 
-template <int LOGT>
+template <int LOGT, int NB = kSwzBuffers>
 struct SwzKvSmem {
   static constexpr uint32_t kHalf = 4u << LOGT;  // keys (or payloads) of one tile
   static constexpr uint32_t kSet = 2 * kHalf;
-  static constexpr size_t kBytes = 1024 + size_t(kSwzBuffers) * kSet + 8 * kSwzBuffers;
+  static constexpr size_t kBytes = 1024 + size_t(NB) * kSet + 8 * NB;
 };
 
 // One pair of the window's lowest layer where the lane may hold the pair in
@@ -271,20 +271,22 @@ __device__ __forceinline__ void ce_kv_flip(uint32_t& a, uint32_t& b, uint32_t& v
   cswap<uint32_t, true>(ASC ? (up < lo) : (up > lo), a, b, va, vb);
 }
 
-template <int LOGT>
-__global__ void __launch_bounds__(1 << (LOGT - 4), (LOGT <= 12) ? 2 : 1)
+// NB tile buffers per CTA: three (two CTAs per SM for 2^12-pair tiles), or
+// two (three CTAs per SM).
+template <int LOGT, int NB = kSwzBuffers>
+__global__ void __launch_bounds__(1 << (LOGT - 4), (LOGT <= 12) ? (NB == 2 ? 3 : 2) : 1)
     darm_merge_swz_kv_kernel(const __grid_constant__ PassParams P, const __grid_constant__ CUtensorMap tmk,
                              const __grid_constant__ CUtensorMap tmv) {
   static_assert(LOGT == 12 || LOGT == 13, "tiles of 2^12 or 2^13 pairs");
   using K = uint32_t;
   constexpr int LOGE = 4;
   constexpr int E = 1 << LOGE;
-  using SK = SwzKvSmem<LOGT>;  // a tile's keys (or payloads): one box of 2^(LOGT-5) <= 256 rows
+  using SK = SwzKvSmem<LOGT, NB>;  // a tile's keys (or payloads): one box of 2^(LOGT-5) <= 256 rows
   extern __shared__ __align__(1024) unsigned char swz_smem[];
   const uint32_t sraw = smem_addr(swz_smem);
   const uint32_t sbase = (sraw + 1023u) & ~1023u;
   unsigned char* sbuf = swz_smem + (sbase - sraw);
-  const uint32_t bar0 = sbase + uint32_t(kSwzBuffers) * SK::kSet;
+  const uint32_t bar0 = sbase + uint32_t(NB) * SK::kSet;
   const uint32_t tid = threadIdx.x;
   const uint32_t ntiles = P.nblocks;
   const uint32_t p = P.rounds[0].p;
@@ -326,13 +328,13 @@ __global__ void __launch_bounds__(1 << (LOGT - 4), (LOGT <= 12) ? 2 : 1)
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmk) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmv) : "memory");
 #pragma unroll
-    for (int b = 0; b < kSwzBuffers; ++b) mbar_init(bar0 + 8u * uint32_t(b), 1);
+    for (int b = 0; b < NB; ++b) mbar_init(bar0 + 8u * uint32_t(b), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   uint32_t pending = 0;
 #pragma unroll
-  for (int b = 0; b < kSwzBuffers; ++b) {
+  for (int b = 0; b < NB; ++b) {
     const uint32_t tl = tile + uint32_t(b) * gridDim.x;
     if (tl < ntiles) {
       if (tid == 0) issue_load(tl, b);
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(1 << (LOGT - 4), (LOGT <= 12) ? 2 : 1)
     if (!mbar_wait_bounded(bar, (phase >> b) & 1u)) {
       if (tid == 0 && P.status != nullptr) atomicOr(P.status, int(kStatusTimeout));
 #pragma unroll
-      for (int q = 0; q < kSwzBuffers; ++q)
+      for (int q = 0; q < NB; ++q)
         if ((pending >> q) & 1u) mbar_wait_bounded(bar0 + 8u * uint32_t(q), (phase >> q) & 1u);
       if (tid == 0) bulk_wait_all();
       return;
@@ -457,9 +459,9 @@ __global__ void __launch_bounds__(1 << (LOGT - 4), (LOGT <= 12) ? 2 : 1)
       __syncthreads();
       if constexpr (IDX == 0) {
         // the previous tile's buffers: once its stores have read them, load
-        // the tile kSwzBuffers - 1 steps ahead of this one into them
-        const uint32_t nt = tile + uint32_t(kSwzBuffers - 1) * gridDim.x;
-        const int pb = (b == 0) ? kSwzBuffers - 1 : b - 1;
+        // the tile NB - 1 steps ahead of this one into them
+        const uint32_t nt = tile + uint32_t(NB - 1) * gridDim.x;
+        const int pb = (b == 0) ? NB - 1 : b - 1;
         if (!first && nt < ntiles) {
           if (tid == 0) {
             bulk_wait_read_all();
@@ -472,7 +474,7 @@ __global__ void __launch_bounds__(1 << (LOGT - 4), (LOGT <= 12) ? 2 : 1)
     });
     if (tid == 0) issue_store(at.start, b);
     first = false;
-    b = (b + 1 == kSwzBuffers) ? 0 : b + 1;
+    b = (b + 1 == NB) ? 0 : b + 1;
   }
   if (tid == 0) bulk_wait_all();
 }

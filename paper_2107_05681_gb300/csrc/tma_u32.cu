@@ -28,10 +28,11 @@ KernelEntry swz_entry(size_t* smem_bytes) {
   return KernelEntry{reinterpret_cast<const void*>(&darm_merge_swz_kernel<LOGT>), 1 << (LOGT - 5)};
 }
 
-template <int LOGT>
+template <int LOGT, int NB = kSwzBuffers>
 KernelEntry swz_kv_entry(size_t* smem_bytes) {
-  if (smem_bytes) *smem_bytes = SwzKvSmem<LOGT>::kBytes;
-  return KernelEntry{reinterpret_cast<const void*>(&darm_merge_swz_kv_kernel<LOGT>), 1 << (LOGT - 4)};
+  if (smem_bytes) *smem_bytes = SwzKvSmem<LOGT, NB>::kBytes;
+  return KernelEntry{reinterpret_cast<const void*>(&darm_merge_swz_kv_kernel<LOGT, NB>),
+                     1 << (LOGT - 4)};
 }
 
 template <bool V, int LOGE, int LOGT>
@@ -51,6 +52,10 @@ KernelEntry tma_merge_shfl_kernel_u32(int loge, int logt, int ns, int var, size_
 
 KernelEntry tma_merge_kernel_u32(bool has_vals, int loge, int logt, int ns, int var,
                                  size_t* smem_bytes) {
+  if (ns == 4) {  // in place, two buffers per CTA (more CTAs per SM)
+    if (has_vals && loge == 4 && logt == 12) return swz_kv_entry<12, 2>(smem_bytes);
+    return KernelEntry{nullptr, 0};
+  }
   if (ns == 3) {  // one form: the direction is uniform per tile
     if (!has_vals && loge == 5 && logt == 14) return swz_entry<14>(smem_bytes);
     if (!has_vals && loge == 5 && logt == 13) return swz_entry<13>(smem_bytes);
@@ -102,6 +107,7 @@ void for_each_tma_kernel_u32(void (*fn)(const void*, void*), void* ctx) {
   fn(tma_merge_kernel_u32(false, 5, 13, 3, 0, nullptr).fn, ctx);
   fn(tma_merge_kernel_u32(true, 4, 12, 3, 0, nullptr).fn, ctx);
   fn(tma_merge_kernel_u32(true, 4, 13, 3, 0, nullptr).fn, ctx);
+  fn(tma_merge_kernel_u32(true, 4, 12, 4, 0, nullptr).fn, ctx);
   for (int var = 0; var < 2; ++var) {
     fn(tma_merge_shfl_kernel_u32(5, 14, 2, var, nullptr).fn, ctx);
     fn(tma_merge_shfl_kernel_u32(5, 13, 2, var, nullptr).fn, ctx);

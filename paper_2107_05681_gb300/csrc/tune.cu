@@ -101,7 +101,7 @@ int darm_autotune(int dtype, size_t n, int has_vals, const char* db_path) {
     for (int e1 = base.e1 - 1; e1 <= base.e1; ++e1)
       for (int e2 : e2_cand)
         for (int w2 = 1; w2 <= 2; ++w2)
-          for (int tma = 0; tma <= 3; ++tma) {
+          for (int tma = 0; tma <= 4; ++tma) {
             Tuning tn = base;
             tn.tma = tma;
             tn.tm = 0;  // one tile size here; a smaller merge tile is tried below

@@ -171,7 +171,7 @@ class Kernel:
             self.kind = "window2_tma"
         elif L["win2"]:
             self.kind = "window2"
-        elif L["tma"] == 3:
+        elif L["tma"] in (3, 4):
             self.kind = "swz_merge"
         elif L["tma"]:
             self.kind = "tma_merge"

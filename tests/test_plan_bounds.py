@@ -41,7 +41,7 @@ def _tuner_candidates(hv):
         for e1 in (base_e1 - 1, base_e1):
             for e2 in (3, 4, 5):
                 for w2 in (1, 2):
-                    for tma in (0, 1, 2, 3):
+                    for tma in (0, 1, 2, 3, 4):
                         for shfl in (0, 1, 3):
                             for tm in (0, t - 1):
                                 yield (t, e1, e2, 8, w2, tma, shfl, tm)
