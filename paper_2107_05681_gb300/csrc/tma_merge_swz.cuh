@@ -1,6 +1,7 @@
-// tma_merge_swz.cuh - merge pass of 32-bit keys (no payload) that works on
-// its tiles in place, in swizzled shared memory, and writes them back with
-// bulk tensor stores.
+// tma_merge_swz.cuh - merge passes of 32-bit keys that work on their tiles
+// in place, in swizzled shared memory, and write them back with bulk tensor
+// stores: keys alone (32 per thread, first kernel) and keys with a 32-bit
+// payload (16 pairs per thread, second kernel, below).
 //
 // The merge pass of a stage k > T runs layers T/2 .. 1 on every tile of
 // T = 2^LOGT keys, 32 keys per thread, in three rounds: window bits

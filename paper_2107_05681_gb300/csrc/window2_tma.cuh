@@ -20,8 +20,8 @@
 //     above), so one box of 16 x 1 x 2^e x 2^e x 1 is one block, dense in
 //     shared memory in local-index order (no swizzle);
 //   - persistent CTAs keep three block buffers: blocks stream in two ahead,
-//     both rounds read and write the thread's own 32 keys in place, and one
-//     thread hands the finished block to a bulk tensor store;
+//     both rounds read and write the thread's own 2^e elements in place,
+//     and one thread hands the finished block to a bulk tensor store;
 //   - round 0 (registers on the top window) puts 32 consecutive words on a
 //     warp's lanes.  In round 1 (registers on the bottom window) a warp's two
 //     half-warps sit 2^(4+e) words apart, on the same 16 banks; so lanes 16..31
@@ -29,7 +29,9 @@
 //     window position r ^ 1), which moves them to the other 16 banks.  That
 //     swap reverses which register of a pair holds the lower index only in
 //     the layer of the window's lowest bit: there those lanes exchange the
-//     roles of min and max (two selects per pair).
+//     roles of min and max (keys alone: two selects per pair; with a
+//     payload: the strict swap test reads the pair's operands in the other
+//     order).
 // The direction (bit k of the index) lies above the block: uniform per
 // block, so the two forms are the same code.  Waits are bounded as in the
 // merge kernels.
