@@ -32,6 +32,7 @@ int occupancy_grid(const void* fn, int threads, size_t smem) {
 }
 
 constexpr int kTinyThreadsLog2 = 7;
+constexpr uint32_t kPaddingThreads = 256;
 
 }  // namespace
 
@@ -90,8 +91,15 @@ int batch_append(BatchTables& bt, KeyKind kk, bool has_vals, const Tuning& tn, i
       if (s.c >= e) order.push_back(&s);
     std::stable_sort(order.begin(), order.end(),
                      [](const BatchSeg* a, const BatchSeg* b) { return a->c > b->c; });
-    // tile blocks, longest segments first
+    // tile blocks, longest segments first.  A block of a segment longer
+    // than the tile that lies wholly beyond the segment's real length holds
+    // only sentinels: every compare-exchange of the tile's stages meets two
+    // equal keys and equal payloads and, swaps being strict, moves nothing,
+    // so the block's tile-pass result is the sentinel at every position.
+    // Such blocks go to a launch of their own that only writes that result
+    // (a tile launch with no rounds).
     const int nr_full = rounds_to(t);
+    std::vector<SegBlock> padding;
     size_t i = 0;
     while (i < order.size()) {
       const int c = order[i]->c;
@@ -105,7 +113,12 @@ int batch_append(BatchTables& bt, KeyKind kk, bool has_vals, const Tuning& tn, i
           B.nrounds = uint8_t(nr_full);
           B.final_pass = (c == t) ? 1 : 0;
           B.fill = 1;
-          bt.blocks.push_back(B);
+          if (c > t && (uint64_t(b) << t) >= order[i]->len) {
+            B.nrounds = 0;
+            padding.push_back(B);
+          } else {
+            bt.blocks.push_back(B);
+          }
         }
         ++i;
       } else {
@@ -155,6 +168,22 @@ int batch_append(BatchTables& bt, KeyKind kk, bool has_vals, const Tuning& tn, i
       bt.launches.push_back(L);
       bt.block_off.push_back(block0);
       bt.slot_off.push_back(slot0);
+    }
+    if (!padding.empty()) {
+      Launch L{};
+      L.kind = PASS_TILE;
+      L.fixed = false;
+      L.variant = pick(PASS_TILE);
+      L.threads = kPaddingThreads;
+      L.grid = uint32_t(padding.size());
+      L.P.b = L.P.c = L.P.w0 = uint32_t(t);
+      L.P.log2cap = uint32_t(t);
+      L.P.map_in = map_in;
+      L.P.nrounds = 0;  // no network: the launch writes the sentinel result
+      bt.block_off.push_back(bt.blocks.size());
+      bt.slot_off.push_back(slot0);
+      bt.blocks.insert(bt.blocks.end(), padding.begin(), padding.end());
+      bt.launches.push_back(L);
     }
     // capacities 2 .. 2^(e-1): one thread sorts a whole segment in registers
     for (int c = e - 1; c >= 1; --c) {

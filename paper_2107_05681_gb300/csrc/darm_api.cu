@@ -36,6 +36,29 @@ const void* fixed_kernel_fn(KeyKind kk, bool has_vals, int loge, int logt, int v
   return e.fn;
 }
 
+// The tile-pass blocks of batched segments that lie wholly beyond their
+// segment's real length (a tile launch with no rounds; batch.cu).  Every
+// key of such a block is the sentinel, so the tile's network moves nothing
+// there and its result is the sentinel key (all ones in the sort's internal
+// key order: the segment is longer than the tile, its later passes read
+// keys unmapped) and payload 0xFFFFFFFF at each of the block's 2^b
+// positions.  One CTA per table entry writes it in 16-byte stores (segment
+// offsets are multiples of 4 elements).
+template <typename K>
+__global__ void darm_padding_tile_kernel(const __grid_constant__ PassParams P) {
+  const SegBlock B = P.blocks[blockIdx.x];
+  const uint64_t at = P.slots[B.first_slot].base + (uint64_t(B.blk_in_seg) << P.b);
+  const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
+  uint4* k4 = reinterpret_cast<uint4*>(static_cast<K*>(P.keys) + at);
+  const uint32_t kvec = uint32_t((uint64_t(sizeof(K)) << P.b) / 16u);
+  for (uint32_t i = threadIdx.x; i < kvec; i += blockDim.x) k4[i] = ones;
+  if (P.vals != nullptr) {
+    uint4* v4 = reinterpret_cast<uint4*>(P.vals + at);
+    const uint32_t vvec = (1u << P.b) / 4u;
+    for (uint32_t i = threadIdx.x; i < vvec; i += blockDim.x) v4[i] = ones;
+  }
+}
+
 // Tensor map of `rows` rows of 32 uint32 keys (128 bytes) from `keys`,
 // read and written in boxes of `box_rows` rows with the 128-byte swizzle
 // (the swizzled in-place merge pass).
@@ -81,8 +104,11 @@ int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_
     P.keys = keys;
     P.vals = vals;
     P.status = g_ctx.d_status;
+    const bool padding = (L.kind == PASS_TILE && L.P.nrounds == 0);
     const void* fn =
-        L.win2t ? window2_tma_kernel_u32(has_vals, nullptr).fn
+        padding ? ((kk == KEY_U32) ? reinterpret_cast<const void*>(&darm_padding_tile_kernel<uint32_t>)
+                                   : reinterpret_cast<const void*>(&darm_padding_tile_kernel<uint64_t>))
+        : L.win2t ? window2_tma_kernel_u32(has_vals, nullptr).fn
         : L.win1 ? window1_kernel(kk == KEY_U64, has_vals, L.loge, int(L.P.c)).fn
         : L.win2 ? ((kk == KEY_U32) ? window2_kernel_u32(has_vals, L.loge, int(L.P.c), L.variant)
                                   : window2_kernel_u64(has_vals, L.loge, int(L.P.c), L.variant)).fn

@@ -87,6 +87,42 @@ def test_edge_segments(darm):
             assert_equal("payload", gv, ev)
 
 
+@pytest.mark.parametrize("entry", ["segmented_sort", "segmented_sort_noalloc"])
+@pytest.mark.parametrize("variant", ["divergent", "melded"])
+@pytest.mark.parametrize("vals", [False, True])
+def test_tile_blocks_wholly_in_padding(darm, entry, variant, vals):
+    """Segments longer than the tile whose real length ends just past half the
+    capacity, on a tile boundary (keys- and key-value tiles are 2^14 and 2^13
+    elements), one past it, or at zero: their tile blocks beyond the length
+    hold only sentinels and go to a launch of their own that writes the
+    sentinel result without running the network.  The padding starts as
+    zeros (payload 0x5A5A5A5A), which would sort first and surface in the
+    result if such a block were not written; mixed directions."""
+    caps = [65536, 65536, 65536, 65536, 65536, 32768, 32768, 32768, 16384, 16384, 65536]
+    lens = [32769, 40960, 49153, 0, 65536, 16385, 24576, 1, 8193, 16384, 57344]
+    offs = np.zeros(len(caps) + 1, np.uint64)
+    offs[1:] = np.cumsum(caps)
+    total = int(offs[-1])
+    # real keys in 1 .. 2^20: neither sentinel (0 descending, 2^32 - 1 ascending)
+    keys = synth.uniform_u32(0x9AD5, total) % np.uint32(1 << 20) + np.uint32(1)
+    vv = np.arange(total, dtype=np.uint32)
+    for o, c, n in zip(offs[:-1], caps, lens):
+        keys[int(o) + n:int(o) + c] = 0
+        vv[int(o) + n:int(o) + c] = 0x5A5A5A5A
+    desc = np.array([i % 2 for i in range(len(caps))], np.uint8)
+    s = synth.Segments(keys, vv, offs, np.array(lens, np.uint32), desc)
+    ek, ev = _expect(s, vals)
+    darm.device_status()  # clear a status latched by an earlier call
+    k = to_dev(keys)
+    v = to_dev(vv) if vals else None
+    getattr(darm, entry)(k, v, offs, s.lengths, variant=variant, seg_desc=desc)
+    gk = k.cpu().numpy()
+    assert_equal("keys", gk, ek)
+    if vals:
+        assert_equal("payload", v.cpu().numpy(), ev)
+    assert darm.device_status() == darm.OK
+
+
 def test_sentinel_collision_is_reported(darm):
     segs = synth.cfg4_segments(seed=24, num_segments=20, min_len=100, max_len=3000)
     keys = segs.keys.copy()
