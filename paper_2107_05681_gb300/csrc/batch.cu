@@ -241,21 +241,37 @@ int batch_append(BatchTables& bt, KeyKind kk, bool has_vals, const Tuning& tn, i
   tp.tma = 0;  // the whole-array shapes; merges are given the bulk-copy kernel below
   if (!plan_array(shape, kk, has_vals, p, tp, variant, 0, 0, g_ctx.smem_limit))
     return DARM_ERR_INVALID_ARG;
+  // Stage p's comparators stay inside aligned blocks of 2^p elements.  One
+  // that starts at or beyond a segment's real length held only sentinels
+  // after the tile pass (whose padding-only blocks store them) and keeps
+  // them through every stage below the one whose block reaches the length:
+  // its compare-exchanges meet equal elements and, the swaps being strict,
+  // move nothing.  A block of a pass of stage p inside such a 2^p block is
+  // left out of the launch, unless the pass is the segment's last (which
+  // also maps the keys back for output).  A pass block's elements share
+  // their index bits >= p (its own bits, the window bits and the bits
+  // between them all lie below p), so the block's first element decides.
   for (const Launch& L0 : shape) {
     if (L0.kind == PASS_TILE || L0.P.rounds[0].p != p) continue;
     const size_t bfirst = bt.blocks.size();
+    const uint32_t nmid = L0.P.w0 - L0.P.c;
     for (size_t j = 0; j < act.size(); ++j) {
+      const bool final_pass = (L0.kind == PASS_MERGE && act[j]->c == p);
       for (uint32_t b = 0; b < (1u << (act[j]->c - int(L0.P.b))); ++b) {
+        const uint64_t g0 = (uint64_t(b & ((1u << nmid) - 1u)) << L0.P.c) |
+                            (uint64_t(b >> nmid) << (L0.P.w0 + L0.P.s));
+        if (!final_pass && ((g0 >> p) << p) >= act[j]->len) continue;
         SegBlock B{};
         B.first_slot = sl[j];
         B.blk_in_seg = b;
         B.log2cap = uint8_t(act[j]->c);
         B.nrounds = uint8_t(L0.P.nrounds);
-        B.final_pass = (L0.kind == PASS_MERGE && act[j]->c == p) ? 1 : 0;
+        B.final_pass = final_pass ? 1 : 0;
         B.fill = 0;
         bt.blocks.push_back(B);
       }
     }
+    if (bt.blocks.size() == bfirst) continue;  // every block of the pass is padding
     Launch L = L0;
     // the window kernels with compile-time shapes address whole arrays only
     L.win2 = false;

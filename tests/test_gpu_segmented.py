@@ -95,11 +95,15 @@ def test_tile_blocks_wholly_in_padding(darm, entry, variant, vals):
     capacity, on a tile boundary (keys- and key-value tiles are 2^14 and 2^13
     elements), one past it, or at zero: their tile blocks beyond the length
     hold only sentinels and go to a launch of their own that writes the
-    sentinel result without running the network.  The padding starts as
-    zeros (payload 0x5A5A5A5A), which would sort first and surface in the
-    result if such a block were not written; mixed directions."""
-    caps = [65536, 65536, 65536, 65536, 65536, 32768, 32768, 32768, 16384, 16384, 65536]
-    lens = [32769, 40960, 49153, 0, 65536, 16385, 24576, 1, 8193, 16384, 57344]
+    sentinel result without running the network, and the blocks of later
+    stages' window and merge passes that lie in a 2^p block of padding are
+    left out (lengths at 2^14 and 3 x 2^14 end exactly on such a block).
+    The padding starts as zeros (payload 0x5A5A5A5A), which would sort first
+    and surface in the result if such a block were not written; mixed
+    directions."""
+    caps = [65536, 65536, 65536, 65536, 65536, 32768, 32768, 32768, 16384, 16384, 65536,
+            65536, 32768]
+    lens = [32769, 40960, 49153, 0, 65536, 16385, 24576, 1, 8193, 16384, 57344, 49152, 16384]
     offs = np.zeros(len(caps) + 1, np.uint64)
     offs[1:] = np.cumsum(caps)
     total = int(offs[-1])
