@@ -940,6 +940,10 @@ def main():
                          "whole_sort_frac": whole_sort_gbs / peak,
                          "pass_ms": {k: statistics.mean(v) for k, v in per_kind.items()},
                          "pass_share": {k: totals[k] / sum(totals.values()) for k in totals},
+                         "pass_timing": "each launch of the array's plan timed alone with CUDA "
+                                        "events on its stream (plan order, whole-array launches); "
+                                        "the timed sorts of 2^22 elements or more run the two "
+                                        "halves' passes concurrently on two streams",
                          **({"note": "one tile on one SM: every stage in one launch, bound "
                                      "by latency, not by HBM"} if passes == 1 else {})},
             "clocks": clk,

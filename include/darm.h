@@ -114,6 +114,17 @@ int darm_device_status(int* status);
 
 /* ---- whole-array sort (Fig. 1, one array of n = 2^m elements) ---------- */
 
+/* Every comparator of stages 2 .. n/2 stays inside one half of the array.
+ * Arrays of 2^22 elements or more are therefore sorted in a split schedule:
+ * the second half's tile pass and stages run on a stream owned by the
+ * library, concurrently with the first half's on `stream`, and the final
+ * stage runs on `stream` once both are done.  Work enqueued on `stream`
+ * before the call happens before both halves, and work enqueued on it after
+ * the call happens after the whole sort, as for any stream-ordered call.
+ * Calls are serialised while they enqueue (the library stream's fork and
+ * join events are shared).  The result is the one network of Fig. 1 over
+ * the whole array. */
+
 /* uint32 keys, optional uint32 payload. */
 int darm_bitonic_sort(uint32_t* keys, uint32_t* vals, size_t n, int dir,
                       int variant, void* stream);
@@ -452,8 +463,10 @@ int darm_plan_describe(int dtype, size_t n, int has_vals, int variant, char* buf
 int darm_plan_dump(int dtype, size_t n, int has_vals, int variant, const int32_t* tuning,
                    size_t smem_limit, int32_t* out, int cap, int* count);
 
-/* Profiling run of a whole-array sort: the same launches as the plain call,
- * with a CUDA event pair recorded on `stream` around each one.  Synchronises
+/* Profiling run of a whole-array sort: the launches of the array's plan in
+ * plan order, all on `stream` (arrays of 2^22 elements or more: the whole
+ * array's passes, not the split schedule of the plain call), with a CUDA
+ * event pair recorded on `stream` around each one.  Synchronises
  * the stream, then writes for launch i < cap: ms[i] = its device time and
  * kind[i] = 0 tile pass, 1 window pass, 2 merge pass; *count = launches.
  * The keys are sorted exactly as by the plain call. */

@@ -500,7 +500,9 @@ PASS_NAMES = ("tile", "window", "merge")
 
 def sort_profile(keys, vals=None, descending: bool = False, variant="melded", stream=None):
     """Sort in place like sort(), timing each kernel launch with CUDA events
-    on the launching stream.  Returns a list of (pass name, milliseconds)."""
+    on the launching stream (the plan's launches in plan order on one stream,
+    without the split schedule of large arrays).  Returns a list of (pass
+    name, milliseconds)."""
     import torch
     dt = {torch.uint32: U32, torch.float32: F32, torch.uint64: U64}.get(keys.dtype)
     if dt is None or not keys.is_cuda or not keys.is_contiguous():

@@ -98,8 +98,14 @@ static bool encode_window2_blocks(CUtensorMap* tm, void* base, uint32_t nblocks,
 
 int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_t* vals,
                 cudaStream_t stream, bool count) {
+  return launch_range(plan.data(), plan.data() + plan.size(), kk, keys, vals, stream, count);
+}
+
+int launch_range(const Launch* first, const Launch* last, KeyKind kk, void* keys, uint32_t* vals,
+                 cudaStream_t stream, bool count) {
   const bool has_vals = vals != nullptr;
-  for (const Launch& L : plan) {
+  for (const Launch* it = first; it != last; ++it) {
+    const Launch& L = *it;
     PassParams P = L.P;
     P.keys = keys;
     P.vals = vals;
@@ -194,12 +200,99 @@ int check_common(const void* keys, const void* vals, size_t n, int dir, int vari
   return -1;  // proceed
 }
 
+// Whole arrays of 2^kSplitMinLog2 elements or more run split: every
+// comparator of stages 2 .. 2^(m-1) stays inside one half of the array, so
+// the two halves go through the tile pass and those stages at the same time,
+// the first on the caller's stream and the second on the library's split
+// stream (the ALU-bound tile pass of one half then runs beside the HBM-bound
+// passes of the other), and the final stage runs over the whole array once
+// both are done.  Every comparator, with its direction, is the whole
+// array's: the halves' passes take their directions from their index in the
+// whole array (dir_base, log2cap = m).
+constexpr int kSplitMinLog2 = 22;
+constexpr int kSplitVariantTag = 0x100;  // plan-cache key of a split plan
+
+// The split plan, cached beside the whole-array plans: for each half h its
+// tile pass and stages 2^(t+1) .. 2^(m-1) (entries [h * per, (h + 1) * per)),
+// then the final stage's launches.  Returns nullptr where the array does
+// not split (a plan the split does not fit).
+const std::vector<Launch>* cached_split_plan(KeyKind kk, bool hv, int m, int variant, uint32_t map,
+                                             size_t* per) {
+  const Tuning tn = tuning_for(kk, hv, m);
+  const std::vector<Launch>* full = cached_plan(kk, hv, m, variant, map, map);
+  if (!full || full->empty() || full->front().kind != PASS_TILE) return nullptr;
+  PlanKey key{int(kk), int(hv), m, variant | kSplitVariantTag, map, map, tn.t, tn.e1, tn.e2, tn.c2,
+              tn.w2 * 16 + tn.tma + tn.shfl * 256 + tn.em * 1024 + tn.tm * 8192,
+              tn.var[0] * 4 + tn.var[1] * 2 + tn.var[2]};
+  std::lock_guard<std::mutex> lk(g_ctx.mu);
+  auto it = g_ctx.plans.find(key);
+  if (it == g_ctx.plans.end()) {
+    std::vector<Launch> out;
+    std::vector<Launch> hplan;
+    const Launch& tile = full->front();
+    const int t = int(tile.P.b);
+    // the half-size plan with the whole array's tuning starts where the
+    // whole array's tile pass ends
+    const bool ok = tile.P.work_counter == nullptr && m - 1 > t &&
+                    plan_array(hplan, kk, hv, m - 1, tn, variant, map, 0u, g_ctx.smem_limit) &&
+                    !hplan.empty() && hplan.front().kind == PASS_TILE && hplan.front().P.b == tile.P.b;
+    if (ok) {
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t off = uint32_t(h) << (m - 1);
+        Launch T = tile;
+        T.grid = 1u << (m - 1 - t);
+        T.P.dir_base = off;
+        out.push_back(T);
+        for (size_t i = 1; i < hplan.size(); ++i) {
+          Launch L = hplan[i];
+          L.P.log2cap = uint32_t(m);
+          L.P.dir_base = off;
+          out.push_back(L);
+        }
+      }
+      for (size_t i = 1; i < full->size(); ++i)
+        if (int((*full)[i].P.rounds[0].p) == m) out.push_back((*full)[i]);
+    }
+    it = g_ctx.plans.emplace(key, std::move(out)).first;
+  }
+  if (it->second.empty()) return nullptr;
+  *per = 0;
+  for (size_t i = 1; i < it->second.size() && it->second[i].kind != PASS_TILE; ++i) *per = i;
+  *per += 1;
+  return &it->second;
+}
+
 int sort_device(KeyKind kk, bool f32, void* keys, uint32_t* vals, size_t n, int dir, int variant,
                 cudaStream_t stream) {
   const int rc = check_common(keys, vals, n, dir, variant);
   if (rc >= 0) return rc;
   const int m = log2_exact(n);
   const uint32_t map = (f32 ? kMapF32 : 0u) | (dir == DARM_DESC ? kMapComplement : 0u);
+  if (m >= kSplitMinLog2) {
+    size_t per = 0;
+    const std::vector<Launch>* sp = cached_split_plan(kk, vals != nullptr, m, variant, map, &per);
+    if (sp) {
+      const Launch* L0 = sp->data();
+      const size_t hn = size_t(1) << (m - 1);
+      const size_t ksz = (kk == KEY_U64) ? 8 : 4;
+      cudaStream_t s2 = g_ctx.split_stream;
+      // one split sort enqueues at a time: the fork and join events are shared
+      static std::mutex split_mu;
+      std::lock_guard<std::mutex> lk(split_mu);
+      if (cudaEventRecord(g_ctx.split_fork_ev, stream) != cudaSuccess ||
+          cudaStreamWaitEvent(s2, g_ctx.split_fork_ev, 0) != cudaSuccess)
+        return DARM_ERR_CUDA;
+      int r = launch_range(L0, L0 + per, kk, keys, vals, stream);
+      if (r != DARM_OK) return r;
+      r = launch_range(L0 + per, L0 + 2 * per, kk, static_cast<char*>(keys) + hn * ksz,
+                       vals ? vals + hn : nullptr, s2);
+      if (r != DARM_OK) return r;
+      if (cudaEventRecord(g_ctx.split_join_ev, s2) != cudaSuccess ||
+          cudaStreamWaitEvent(stream, g_ctx.split_join_ev, 0) != cudaSuccess)
+        return DARM_ERR_CUDA;
+      return launch_range(L0 + 2 * per, L0 + sp->size(), kk, keys, vals, stream);
+    }
+  }
   const std::vector<Launch>* plan = cached_plan(kk, vals != nullptr, m, variant, map, map);
   if (!plan) return DARM_ERR_INVALID_ARG;
   return launch_plan(*plan, kk, keys, vals, stream);
@@ -278,6 +371,10 @@ int darm_sort_init(int device, size_t workspace_bytes) {
     return DARM_ERR_CUDA;
   if (cudaEventCreateWithFlags(&g_ctx.host_join_ev, cudaEventDisableTiming) != cudaSuccess)
     return DARM_ERR_CUDA;
+  if (cudaStreamCreateWithFlags(&g_ctx.split_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g_ctx.split_fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g_ctx.split_join_ev, cudaEventDisableTiming) != cudaSuccess)
+    return DARM_ERR_CUDA;
   if (workspace_bytes) {
     if (cudaMalloc(&g_ctx.ws, workspace_bytes) != cudaSuccess) return DARM_ERR_OOM;
     g_ctx.ws_bytes = workspace_bytes;
@@ -302,6 +399,12 @@ int darm_sort_finalize(void) {
   if (g_ctx.host_join_ev) cudaEventDestroy(g_ctx.host_join_ev);
   g_ctx.host_stream2 = nullptr;
   g_ctx.host_join_ev = nullptr;
+  if (g_ctx.split_stream) cudaStreamDestroy(g_ctx.split_stream);
+  if (g_ctx.split_fork_ev) cudaEventDestroy(g_ctx.split_fork_ev);
+  if (g_ctx.split_join_ev) cudaEventDestroy(g_ctx.split_join_ev);
+  g_ctx.split_stream = nullptr;
+  g_ctx.split_fork_ev = nullptr;
+  g_ctx.split_join_ev = nullptr;
   for (cudaEvent_t& e : g_ctx.host_chunk_ev) {
     if (e) cudaEventDestroy(e);
     e = nullptr;

@@ -29,6 +29,9 @@ struct Context {
   cudaStream_t host_stream2 = nullptr;      // tile passes of the second half
   cudaEvent_t host_join_ev = nullptr;       // ... joined back into host_stream
   cudaEvent_t host_chunk_ev[8] = {};        // one per chunk copied
+  cudaStream_t split_stream = nullptr;  // second half of a split whole-array sort
+  cudaEvent_t split_fork_ev = nullptr;  // caller's stream -> split_stream
+  cudaEvent_t split_join_ev = nullptr;  // split_stream -> caller's stream
   void* ws = nullptr;                // workspace of host-buffer sorts
   size_t ws_bytes = 0;
   std::mutex mu;       // plans, tuning table, init/finalize
@@ -47,6 +50,9 @@ const void* fixed_kernel_fn(KeyKind kk, bool has_vals, int loge, int logt, int v
 // counted instead).
 int launch_plan(const std::vector<Launch>& plan, KeyKind kk, void* keys, uint32_t* vals,
                 cudaStream_t stream, bool count = true);
+// The same for the launches [first, last) of a plan.
+int launch_range(const Launch* first, const Launch* last, KeyKind kk, void* keys, uint32_t* vals,
+                 cudaStream_t stream, bool count = true);
 Tuning tuning_for(KeyKind kk, bool has_vals, int m);
 const std::vector<Launch>* cached_plan(KeyKind kk, bool has_vals, int m, int variant,
                                        uint32_t map_in, uint32_t map_out);

@@ -10,6 +10,12 @@ SB1 | SB4 | SB1-R | SB4-R (the synthetic divergent kernels, 1216 blocks),
 kv24 (2^24 uint32 key-value pairs), f32 (2^26 float32 keys),
 pcm26 (PCM of 2^26 uint32 keys in buckets of 4096: one bucket-sort launch and
 105 merge-split layer launches per sort, then one gather launch).
+
+The whole-array workloads (cfg1, kv24, f32) run the array's plan one launch
+at a time in plan order (darm_sort_profile): the same kernels, launch shapes
+and comparators as a sort, but not the split schedule that sorts of 2^22
+elements or more use (two halves on two streams, then the final stage), so
+that a launch's index in the capture names the same pass of every sort.
 """
 import sys
 
@@ -59,7 +65,7 @@ def main(variant="melded", workload="kv24"):
     for _ in range(2):
         K2 = K.clone()
         V2 = V.clone() if V is not None else None
-        darm.sort(K2, V2, variant=variant)
+        darm.sort_profile(K2, V2, variant=variant)
     torch.cuda.synchronize()
     print("ok", darm.launch_count())
 

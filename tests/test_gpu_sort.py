@@ -162,6 +162,37 @@ def test_cfg3_f32_2pow26_full(darm):
     assert_equal("keys", gk.view(np.uint32), ek.view(np.uint32))
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("case", ["u32_kv_22_desc", "u32_keys_23", "f32_22_desc", "u64_kv_22",
+                                  "u64_kv_22_desc"])
+def test_split_whole_array_sorts(darm, case, variant):
+    """Arrays of 2^22 elements and more run their two halves' tile passes and
+    stages below the final one concurrently on two streams, then the final
+    stage over the whole array: keys and payload order under ties against
+    the oracle's single network, ascending and descending, every key kind."""
+    kind, *rest = case.split("_")
+    desc = rest[-1] == "desc"
+    m = int(rest[-2] if desc else rest[-1])
+    n = 1 << m
+    hv = "kv" in rest
+    if kind == "u64":
+        keys = synth.uniform_u64(6100 + m, n) % np.uint64(n // 8)
+    elif kind == "f32":
+        keys = synth.cfg3_f32(0xDA2C0003, n)
+    else:
+        keys = synth.uniform_u32(6200 + m, n) % np.uint32(n // 8)
+    vals = np.arange(n, dtype=np.uint32) if hv else None
+    ek, ev = oracle.bitonic_sort(keys, vals, desc=desc)
+    gk, gv = gpu_sort(darm, keys, vals, desc=desc, variant=variant)
+    if kind == "f32":
+        assert_equal("keys", total_order_u32(gk), total_order_u32(ek))
+    else:
+        assert_equal("keys", gk, ek)
+    if hv:
+        assert_equal("payload", gv, ev)
+    assert darm.device_status() == 0
+
+
 def test_host_buffer_sort(darm):
     n = 1 << 16
     keys = synth.uniform_u32(91, n) % np.uint32(100)
