@@ -16,8 +16,10 @@
 //   3. segments of capacity 2..8 are sorted in registers by one thread each;
 //      capacity-1 segments only receive their sentinel when empty.
 //
-// The whole sequence is captured once per layout as a CUDA graph and replayed
-// on later calls with the same segments, pointers, direction and variant.
+// The segments are dealt into two groups of about equal padded size, each
+// with its own sequence; the two sequences are captured once per layout as
+// one CUDA graph on two streams and replayed on later calls with the same
+// segments, pointers, direction and variant.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -101,12 +103,38 @@ int build_seg_plan(SegPlan& sp, uint32_t* keys, uint32_t* vals, const std::vecto
                    int variant, const Tuning& tn) {
   const bool has_vals = vals != nullptr;
   const KeyKind kk = KEY_U32;
-  int cmax = 0;
-  for (const BatchSeg& s : segs) cmax = std::max(cmax, s.c);
+  // Two groups of segments of about equal padded size (largest first, each
+  // to the lighter group), each with its own launch sequence: the graph
+  // runs the two sequences on two streams, so that one group's passes fill
+  // the other's launch ramps and tails and its HBM-bound passes run beside
+  // the other's ALU-bound tile pass.  Segments are independent, so the
+  // result is each segment's own network.
+  std::vector<BatchSeg> group[2];
+  {
+    std::vector<const BatchSeg*> order;
+    for (const BatchSeg& s : segs)
+      if (s.c >= 1) order.push_back(&s);
+    std::stable_sort(order.begin(), order.end(),
+                     [](const BatchSeg* a, const BatchSeg* b) { return a->c > b->c; });
+    uint64_t load[2] = {0, 0};
+    for (const BatchSeg* s : order) {
+      const int g = (load[1] < load[0]) ? 1 : 0;
+      group[g].push_back(*s);
+      load[g] += uint64_t(1) << s->c;
+    }
+  }
   BatchTables bt;
-  int rc = batch_append(bt, kk, has_vals, tn, variant, segs, 0, 0);
-  for (int p = tn.t + 1; p <= cmax && rc == DARM_OK; ++p)
-    rc = batch_append(bt, kk, has_vals, tn, variant, segs, p, 0);
+  size_t second = 0;  // first launch of group 1
+  int rc = DARM_OK;
+  for (int g = 0; g < 2 && rc == DARM_OK; ++g) {
+    if (g == 1) second = bt.launches.size();
+    int cmax = 0;
+    for (const BatchSeg& s : group[g]) cmax = std::max(cmax, s.c);
+    if (group[g].empty()) continue;
+    rc = batch_append(bt, kk, has_vals, tn, variant, group[g], 0, 0);
+    for (int p = tn.t + 1; p <= cmax && rc == DARM_OK; ++p)
+      rc = batch_append(bt, kk, has_vals, tn, variant, group[g], p, 0);
+  }
   if (rc != DARM_OK) return rc;
 
   // singletons
@@ -141,15 +169,35 @@ int build_seg_plan(SegPlan& sp, uint32_t* keys, uint32_t* vals, const std::vecto
   batch_bind(bt, sp.d_blocks, sp.d_slots, sp.d_counter);
   sp.launches = bt.launches;
 
-  // capture
-  cudaStream_t cs;
+  // capture: group 0 on cs, group 1 on cs2 (forked from cs after the
+  // counters are zeroed, joined back before the singletons)
+  cudaStream_t cs, cs2;
+  cudaEvent_t fork_ev, join_ev;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return DARM_ERR_CUDA;
-  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking) != cudaSuccess) {
     cudaStreamDestroy(cs);
     return DARM_ERR_CUDA;
   }
+  if (cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    cudaStreamDestroy(cs2);
+    return DARM_ERR_CUDA;
+  }
   cudaMemsetAsync(sp.d_counter, 0, ncounters * sizeof(unsigned int), cs);
-  rc = launch_plan(sp.launches, kk, keys, vals, cs, /*count=*/false);
+  const Launch* L0 = sp.launches.data();
+  if (second > 0 && second < sp.launches.size()) {
+    cudaEventRecord(fork_ev, cs);
+    cudaStreamWaitEvent(cs2, fork_ev, 0);
+    rc = launch_range(L0, L0 + second, kk, keys, vals, cs, /*count=*/false);
+    if (rc == DARM_OK)
+      rc = launch_range(L0 + second, L0 + sp.launches.size(), kk, keys, vals, cs2, false);
+    cudaEventRecord(join_ev, cs2);
+    cudaStreamWaitEvent(cs, join_ev, 0);
+  } else {
+    rc = launch_plan(sp.launches, kk, keys, vals, cs, /*count=*/false);
+  }
   if (rc == DARM_OK && sp.n_single) {
     if (launch_singletons(keys, vals, sp.d_single_base, sp.d_single_ld, sp.n_single, cs) !=
         cudaSuccess)
@@ -158,6 +206,9 @@ int build_seg_plan(SegPlan& sp, uint32_t* keys, uint32_t* vals, const std::vecto
   cudaGraph_t graph = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
   cudaStreamDestroy(cs);
+  cudaStreamDestroy(cs2);
+  cudaEventDestroy(fork_ev);
+  cudaEventDestroy(join_ev);
   if (rc != DARM_OK) {
     if (graph) cudaGraphDestroy(graph);
     return rc;
