@@ -204,9 +204,9 @@ int check_common(const void* keys, const void* vals, size_t n, int dir, int vari
 // comparator of stages 2 .. 2^(m-1) stays inside one half of the array, so
 // the two halves go through the tile pass and those stages at the same time,
 // the first on the caller's stream and the second on the library's split
-// stream (the ALU-bound tile pass of one half then runs beside the HBM-bound
-// passes of the other), and the final stage runs over the whole array once
-// both are done.  Every comparator, with its direction, is the whole
+// stream (one half's launches fill the other's launch ramps and tails, and
+// its HBM-bound passes can run beside the other's ALU-bound tile pass), and
+// the final stage runs over the whole array once both are done.  Every comparator, with its direction, is the whole
 // array's: the halves' passes take their directions from their index in the
 // whole array (dir_base, log2cap = m).
 constexpr int kSplitMinLog2 = 22;
